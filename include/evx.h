@@ -1,0 +1,160 @@
+/*
+ * evx.h - C-ABI of the GB300 (sm_103a) semi-implicit Fourier-spectral
+ * Cahn-Hilliard solver (the evoxels method, arXiv 2507.21748).
+ *
+ * The method (paper, Appendix "Microstructure modelling"):
+ *   Eq. (cahn-hilliard)  c_t = div(M grad mu), mu = f'(c) - kappa lap c, here
+ *   with constant mobility M, f'(c) = c^3 - c and kappa the gradient
+ *   coefficient (the paper's 2 gamma0 eps).
+ *   Subsection "Semi-implicit timestepping": the stiff linear operator is
+ *   treated implicitly in Fourier space with the prefactor dt / (1 - dt S),
+ *   S its symbol (S = -M kappa |k|^4), which for the spectral right-hand side
+ *   gives, per step,
+ *       c_hat <- (c_hat - dt M |k|^2 F{c^3 - c}) / (1 + dt M kappa |k|^4).
+ *   Grid: periodic nx*ny*nz voxels of edge h; k_d = 2 pi m / (n_d h) with m the
+ *   signed index.
+ *
+ * Conventions for every entry point
+ *   - Every call returns an evx_status; no exception or abort crosses the ABI.
+ *     On failure the message is available from evx_last_error(g).
+ *   - "device pointer" arguments are CUDA device addresses on the device that
+ *     was current when the grid was created; the caller owns them and keeps
+ *     them alive until the work on the grid's stream that uses them has
+ *     finished. "host pointer" arguments are ordinary (ideally pinned) host
+ *     memory; calls taking host pointers return only after the copy is done.
+ *   - Real fields are float32, C order (x slowest, z fastest), nx*ny*nz values,
+ *     contiguous.
+ *   - A grid owns all of its internal buffers (allocated in evx_grid_create,
+ *     except the adjoint's segment store, allocated by the first
+ *     evx_ch_adjoint call and kept until destroy). One grid is used by one
+ *     host thread at a time.
+ *   - Work is issued on the grid's CUDA stream and is asynchronous unless the
+ *     entry point says it synchronises.
+ *   - Sizes: nx, ny, nz each even, 8 <= n <= 1024, with no prime factor other
+ *     than 2, 3 and 5; otherwise EVX_ERR_SIZE.
+ */
+#ifndef EVX_H
+#define EVX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct evx_grid evx_grid; /* opaque */
+
+typedef enum {
+    EVX_OK = 0,
+    EVX_ERR_ARG = 1,       /* null pointer, non-positive count, bad parameter */
+    EVX_ERR_SIZE = 2,      /* grid size outside the supported set */
+    EVX_ERR_OOM = 3,       /* device allocation failed */
+    EVX_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed */
+    EVX_ERR_NONFINITE = 5, /* a reduction found NaN or Inf in the field */
+    EVX_ERR_STATE = 6      /* call made in the wrong state (e.g. no field set) */
+} evx_status;
+
+/* Scheme parameters: time step dt, mobility M (>= 0), gradient coefficient
+ * kappa (>= 0), voxel edge h (> 0). Appendix "Semi-implicit timestepping". */
+typedef struct {
+    double dt;
+    double M;
+    double kappa;
+    double h;
+} evx_params;
+
+/* Create a grid: validates sizes, allocates the two half-spectrum FP32
+ * buffers (state S and work W, each nx*ny*Zp complex64 with
+ * Zp = roundup(nz/2 + 1, 8)), FP64 scalars, reduction scratch and the
+ * twiddle and wave-number tables. cuda_stream: a cudaStream_t (NULL = the
+ * legacy default stream). *out receives the handle. The grid holds no field
+ * until evx_set_field. */
+evx_status evx_grid_create(int nx, int ny, int nz, evx_params p, void *cuda_stream,
+                           evx_grid **out);
+
+/* Synchronise the grid's stream and free everything the grid owns. NULL is
+ * accepted (no-op). */
+evx_status evx_grid_destroy(evx_grid *g);
+
+/* Replace dt, M, kappa, h (validated as above). Takes effect for work issued
+ * after the call. */
+evx_status evx_set_params(evx_grid *g, evx_params p);
+
+/* Change the stream later work is issued on (the caller orders it against
+ * earlier work). */
+evx_status evx_set_stream(evx_grid *g, void *cuda_stream);
+
+/* Load the initial field from a device pointer d_c (nx*ny*nz float32). The
+ * library forms the spectral state (3D real-to-complex transform of c) and
+ * carries the mean of c separately in FP64 (sum in FP64 of the FP32 input):
+ * the k = 0 Fourier mode never enters an FP32 buffer, so the scheme's mass
+ * (paper: "conserved") is kept exactly. Asynchronous. */
+evx_status evx_set_field(evx_grid *g, const float *d_c);
+
+/* Same from a host pointer; returns after the host buffer has been read. */
+evx_status evx_set_field_host(evx_grid *g, const float *h_c);
+
+/* Write the current real field c(x) (inverse transform + FP64 mean) to the
+ * caller's device buffer d_out (nx*ny*nz float32). Asynchronous. */
+evx_status evx_get_field(evx_grid *g, float *d_out);
+
+/* Same into host memory; synchronises the stream. */
+evx_status evx_get_field_host(evx_grid *g, float *h_out);
+
+/* Advance the state by n_steps >= 0 semi-implicit steps (update above).
+ * Asynchronous: the steps are issued on the grid's stream (as CUDA-graph
+ * launches when profiling is off). */
+evx_status evx_ch_step(evx_grid *g, int n_steps);
+
+/* Ginzburg-Landau energy and mass of the current field, in FP64 (paper:
+ * F_int of subsection "Phase transformations", in the c in [-1, 1] form):
+ *   E    = h^3 sum_x (c^2 - 1)^2 / 4 + h^3 (kappa/2) (1/V) sum_k |k|^2 |c_hat(k)|^2
+ *   mass = h^3 V cbar   (cbar the FP64 mean carried since evx_set_field).
+ * Either output pointer may be NULL. Host outputs; synchronises the stream.
+ * Returns EVX_ERR_NONFINITE if the field holds NaN or Inf. */
+evx_status evx_energy(evx_grid *g, double *E, double *mass);
+
+/* FP64 mean of the field (the carried cbar); host output; synchronises. */
+evx_status evx_mean(evx_grid *g, double *cbar);
+
+/* Discrete adjoint of n_steps steps of the scheme started from d_c0 (device,
+ * nx*ny*nz float32), with the current parameters. Given d_dLdcN = dL/dc_N
+ * (device, same layout) it writes dL/dc_0 to d_dLdc0 (device, caller-owned)
+ * and, if non-NULL, dL/dkappa and dL/dM to host doubles. The forward states
+ * are recomputed from checkpoints taken every ckpt_every steps (>= 1); memory
+ * grows with ckpt_every (about 3 fields per step of a segment). The grid's
+ * own state is overwritten (it holds c_N of the replayed trajectory
+ * afterwards). Synchronises. Recursion:
+ *   lambda_N = dL/dc_N,
+ *   lambda_n = A lambda_{n+1} + (3 c_n^2 - 1) (B lambda_{n+1}),
+ * A, B the convolutions of symbols a = 1/D, b = -dt M |k|^2 / D,
+ * D = 1 + dt M kappa |k|^4; parameter gradients accumulate
+ * <lambda_{n+1}, (dA/dtheta) c_n + (dB/dtheta) g(c_n)> in FP64. */
+evx_status evx_ch_adjoint(evx_grid *g, const float *d_c0, int n_steps, int ckpt_every,
+                          const float *d_dLdcN, float *d_dLdc0, double *dLdkappa,
+                          double *dLdM);
+
+/* Device memory the grid holds, in bytes (buffers + tables + scratch). */
+evx_status evx_footprint(const evx_grid *g, size_t *bytes);
+
+/* Per-pass timing. With profiling on, evx_ch_step issues its kernels
+ * without CUDA graphs and records a CUDA event pair around every pass on the
+ * grid's stream; evx_pass_times (synchronises) returns, for each of the four
+ * step passes (0: x pass + update, 1: y inverse, 2: z C2R + c^3-c + R2C,
+ * 3: y forward), the summed milliseconds and launch counts since the last
+ * reset. ms and counts each hold 4 entries. */
+evx_status evx_set_profiling(evx_grid *g, int on);
+evx_status evx_pass_times(evx_grid *g, double *ms, long long *counts, int reset);
+
+/* Algorithmic bytes one launch of a step pass reads plus writes (each input
+ * and output element once): pass index as in evx_pass_times. */
+evx_status evx_pass_bytes(const evx_grid *g, int pass, double *bytes);
+
+/* Last error message of g (or of the calling thread when g is NULL). */
+const char *evx_last_error(const evx_grid *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVX_H */

@@ -1,0 +1,73 @@
+"""Build libevx.so (the CUDA library behind include/evx.h) in-tree for sm_103a.
+
+Each translation unit is compiled by nvcc in parallel, then linked into
+``paper_2507_21748_gb300/_lib/libevx.so``. No cmake, no torch extension
+machinery: the library is a plain C-ABI shared object.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OUT_DIR = os.path.join(HERE, "_lib")
+LIB = os.path.join(OUT_DIR, "libevx.so")
+SOURCES = ["evx_kernels.cu", "evx_runtime.cu", "evx_adjoint.cu", "evx_conv.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc():
+    cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    return cand
+
+
+def _flags(debug_bounds=False):
+    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+                "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
+    if debug_bounds:
+        f.append("-DEVX_BOUNDS_CHECK")
+    return f
+
+
+def _deps_mtime():
+    m = 0.0
+    for fn in os.listdir(CSRC):
+        m = max(m, os.path.getmtime(os.path.join(CSRC, fn)))
+    m = max(m, os.path.getmtime(os.path.join(HERE, "..", "include", "evx.h")))
+    return m
+
+
+def build_lib(force=False, verbose=False, jobs=None):
+    sources = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+        return LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    nvcc = _nvcc()
+    flags = _flags()
+
+    def compile_one(src):
+        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        cmd = [nvcc] + flags + ["-I", os.path.join(HERE, "..", "include"), "-c",
+                                os.path.join(CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
+        if verbose and (r.stdout or r.stderr):
+            sys.stderr.write(r.stdout + r.stderr)
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=jobs or len(sources)) as ex:
+        objs = list(ex.map(compile_one, sources))
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build_lib(force="-f" in sys.argv, verbose=True))

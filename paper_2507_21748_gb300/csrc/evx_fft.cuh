@@ -1,0 +1,263 @@
+// Device FFT building blocks for the spectral Cahn-Hilliard passes.
+//
+// A CTA holds a tile of `npen` pencils of length L (complex float2) in shared
+// memory; element i of pencil p lives at buf[i*es + p*ps]. A 1D transform
+// along i is a sequence of Stockham (self-sorting) radix stages, one per
+// factor of L (radices 16, 8, 4, 2, 5, 3). Stage s with radix R and
+// Ns = product of earlier radices maps, for j in [0, L/R) with kk = j mod Ns,
+//     v[t] = x[j + t L/R] * w_{Ns R}^{t kk}         (t < R)
+//     y[(j - kk) R + kk + u Ns] = sum_t v[t] w_R^{t u} (u < R)
+// which leaves the result in natural order after the last stage
+// (Stockham autosort; Govindaraju et al., SC'08). Every stage is done in
+// place: each thread loads its butterflies into registers, the CTA
+// synchronises, then writes.
+//
+// Twiddles come from a table tw[m] = exp(-2 pi i m / L), m < L, computed on
+// the host in FP64 and rounded to FP32; w_{Ns R}^{t kk} = tw[t kk L/(Ns R)].
+// DIR = -1 is the forward transform (exp(-i..)), +1 the inverse, both
+// unnormalised.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace evx {
+
+constexpr int NT = 256;           // threads per CTA of every FFT pass
+constexpr int TILE_CAP = 4096;    // max complex elements one fft_tile call transforms
+constexpr int MAX_STAGES = 12;
+
+struct Plan {
+    int n;                 // number of stages
+    int r[MAX_STAGES];     // radix of each stage
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by -i (DIR=-1) or +i (DIR=+1)
+template <int DIR>
+__device__ __forceinline__ float2 mul_i(float2 a) {
+    return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+// multiply by exp(DIR * i pi m / 8) for fixed m (constants of the 16th roots of unity)
+template <int DIR, int m>
+__device__ __forceinline__ float2 w16(float2 a) {
+    constexpr float C1 = 0.92387953251128674f;  // cos(pi/8)
+    constexpr float S1 = 0.38268343236508978f;  // sin(pi/8)
+    constexpr float R2 = 0.70710678118654752f;  // cos(pi/4)
+    constexpr int mm = m & 15;
+    float c, s;  // exp(-i pi mm / 8) = c - i s  (forward); conj for inverse
+    switch (mm) {
+        case 0: return a;
+        case 1: c = C1; s = S1; break;
+        case 2: c = R2; s = R2; break;
+        case 3: c = S1; s = C1; break;
+        case 4: return mul_i<DIR>(a);
+        case 5: c = -S1; s = C1; break;
+        case 6: c = -R2; s = R2; break;
+        case 7: c = -C1; s = S1; break;
+        default: c = 1.f; s = 0.f; break;  // not used (m < 8 in radix-16)
+    }
+    // (a.x + i a.y)(c + i DIR s)
+    const float ds = DIR < 0 ? -s : s;
+    return make_float2(fmaf(a.x, c, -a.y * ds), fmaf(a.x, ds, a.y * c));
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    float2 t2 = cadd(a1, a3), t3 = mul_i<DIR>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+template <int R, int DIR>
+struct Dft;
+
+template <int DIR>
+struct Dft<2, DIR> {
+    __device__ __forceinline__ static void run(float2* v) { dft2<DIR>(v[0], v[1]); }
+};
+template <int DIR>
+struct Dft<4, DIR> {
+    __device__ __forceinline__ static void run(float2* v) { dft4<DIR>(v[0], v[1], v[2], v[3]); }
+};
+template <int DIR>
+struct Dft<8, DIR> {
+    // decimation in time: E = DFT4(even), O = DFT4(odd), X_k = E_k + w8^k O_k
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+        float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+        dft4<DIR>(e0, e1, e2, e3);
+        dft4<DIR>(o0, o1, o2, o3);
+        o1 = w16<DIR, 2>(o1);
+        o2 = w16<DIR, 4>(o2);
+        o3 = w16<DIR, 6>(o3);
+        v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+        v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+        v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+        v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+    }
+};
+template <int DIR>
+struct Dft<16, DIR> {
+    // 4 x 4: E_{n2}[k1] = DFT4_{n1}(a[4 n1 + n2]); twiddle w16^{n2 k1};
+    // X[k1 + 4 k2] = DFT4_{n2}(...)[k2]
+    __device__ __forceinline__ static void run(float2* v) {
+        dft4<DIR>(v[0], v[4], v[8], v[12]);
+        dft4<DIR>(v[1], v[5], v[9], v[13]);
+        dft4<DIR>(v[2], v[6], v[10], v[14]);
+        dft4<DIR>(v[3], v[7], v[11], v[15]);
+        // after dft4 on (v[n2], v[4+n2], v[8+n2], v[12+n2]) slot 4*k1 + n2 holds E_{n2}[k1]
+        v[5] = w16<DIR, 1>(v[5]);
+        v[6] = w16<DIR, 2>(v[6]);
+        v[7] = w16<DIR, 3>(v[7]);
+        v[9] = w16<DIR, 2>(v[9]);
+        v[10] = w16<DIR, 4>(v[10]);
+        v[11] = w16<DIR, 6>(v[11]);
+        v[13] = w16<DIR, 3>(v[13]);
+        v[14] = w16<DIR, 6>(v[14]);
+        // w16^9 = -w16^1
+        v[15] = w16<DIR, 1>(make_float2(-v[15].x, -v[15].y));
+        dft4<DIR>(v[0], v[1], v[2], v[3]);
+        dft4<DIR>(v[4], v[5], v[6], v[7]);
+        dft4<DIR>(v[8], v[9], v[10], v[11]);
+        dft4<DIR>(v[12], v[13], v[14], v[15]);
+        // slot 4*k1 + k2 now holds X[k1 + 4 k2]; transpose to natural order
+        float2 t;
+        t = v[1]; v[1] = v[4]; v[4] = t;
+        t = v[2]; v[2] = v[8]; v[8] = t;
+        t = v[3]; v[3] = v[12]; v[12] = t;
+        t = v[6]; v[6] = v[9]; v[9] = t;
+        t = v[7]; v[7] = v[13]; v[13] = t;
+        t = v[11]; v[11] = v[14]; v[14] = t;
+    }
+};
+template <int DIR>
+struct Dft<3, DIR> {
+    __device__ __forceinline__ static void run(float2* v) {
+        constexpr float H3 = 0.86602540378443865f;  // sin(2 pi / 3)
+        float2 t = cadd(v[1], v[2]);
+        float2 s = csub(v[1], v[2]);
+        float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+        float2 r = mul_i<DIR>(cscale(s, H3));  // DIR i sin(2pi/3) s
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    }
+};
+template <int DIR>
+struct Dft<5, DIR> {
+    __device__ __forceinline__ static void run(float2* v) {
+        constexpr float C1 = 0.30901699437494742f;   // cos(2 pi/5)
+        constexpr float C2 = -0.80901699437494742f;  // cos(4 pi/5)
+        constexpr float S1 = 0.95105651629515357f;   // sin(2 pi/5)
+        constexpr float S2 = 0.58778525229247313f;   // sin(4 pi/5)
+        float2 t1 = cadd(v[1], v[4]), d1 = csub(v[1], v[4]);
+        float2 t2 = cadd(v[2], v[3]), d2 = csub(v[2], v[3]);
+        float2 a0 = v[0];
+        float2 m1 = make_float2(a0.x + C1 * t1.x + C2 * t2.x, a0.y + C1 * t1.y + C2 * t2.y);
+        float2 m2 = make_float2(a0.x + C2 * t1.x + C1 * t2.x, a0.y + C2 * t1.y + C1 * t2.y);
+        // forward: X1 = m1 - i(S1 d1 + S2 d2), X2 = m2 - i(S2 d1 - S1 d2)
+        float2 q1 = mul_i<DIR>(make_float2(S1 * d1.x + S2 * d2.x, S1 * d1.y + S2 * d2.y));
+        float2 q2 = mul_i<DIR>(make_float2(S2 * d1.x - S1 * d2.x, S2 * d1.y - S1 * d2.y));
+        v[0] = make_float2(a0.x + t1.x + t2.x, a0.y + t1.y + t2.y);
+        v[1] = cadd(m1, q1);
+        v[4] = csub(m1, q1);
+        v[2] = cadd(m2, q2);
+        v[3] = csub(m2, q2);
+    }
+};
+
+// Tile descriptor: pencil p, element i at buf[i*es + p*ps].
+struct Tile {
+    float2* buf;
+    int L;
+    int npen;
+    int es;
+    int ps;
+};
+
+// One in-place Stockham stage of radix R. PEN_FAST: consecutive threads take
+// consecutive pencils (tiles whose pencils are adjacent in memory); otherwise
+// consecutive butterflies of one pencil.
+template <int R, int DIR, bool PEN_FAST>
+__device__ __forceinline__ void fft_stage(const Tile& t, int Ns, const float2* __restrict__ tw) {
+    constexpr int KMAX = (TILE_CAP + R * NT - 1) / (R * NT);
+    const int LR = t.L / R;
+    const int nb = LR * t.npen;
+    const int tws = t.L / (Ns * R);
+    float2 v[KMAX][R];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int b = threadIdx.x + k * NT;
+        if (b < nb) {
+            int p, j;
+            if (PEN_FAST) { p = b % t.npen; j = b / t.npen; }
+            else          { j = b % LR;     p = b / LR; }
+            const int kk = j % Ns;
+            const float2* src = t.buf + p * t.ps + j * t.es;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[k][r] = src[r * LR * t.es];
+            if (Ns > 1) {
+                const int step = tws * kk;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = tw[r * step];
+                    if (DIR > 0) w.y = -w.y;
+                    v[k][r] = cmul(v[k][r], w);
+                }
+            }
+            Dft<R, DIR>::run(v[k]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int b = threadIdx.x + k * NT;
+        if (b < nb) {
+            int p, j;
+            if (PEN_FAST) { p = b % t.npen; j = b / t.npen; }
+            else          { j = b % LR;     p = b / LR; }
+            const int kk = j % Ns;
+            float2* dst = t.buf + p * t.ps + ((j - kk) * R + kk) * t.es;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[r * Ns * t.es] = v[k][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Full 1D transform of every pencil of the tile (caller has synchronised;
+// L * npen <= TILE_CAP). Not inlined: one copy serves every kernel.
+template <int DIR, bool PEN_FAST>
+__device__ __noinline__ void fft_tile(const Tile& t, const Plan& pl, const float2* __restrict__ tw) {
+    int Ns = 1;
+    for (int s = 0; s < pl.n; ++s) {
+        const int R = pl.r[s];
+        switch (R) {
+            case 16: fft_stage<16, DIR, PEN_FAST>(t, Ns, tw); break;
+            case 8:  fft_stage<8, DIR, PEN_FAST>(t, Ns, tw); break;
+            case 4:  fft_stage<4, DIR, PEN_FAST>(t, Ns, tw); break;
+            case 2:  fft_stage<2, DIR, PEN_FAST>(t, Ns, tw); break;
+            case 5:  fft_stage<5, DIR, PEN_FAST>(t, Ns, tw); break;
+            case 3:  fft_stage<3, DIR, PEN_FAST>(t, Ns, tw); break;
+            default: break;
+        }
+        Ns *= R;
+    }
+}
+
+}  // namespace evx

@@ -1,0 +1,46 @@
+// Private definition of the evx grid handle, shared by the runtime files.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/evx.h"
+#include "evx_internal.h"
+
+using evx::Plan;
+
+struct AdjStore;  // adjoint segment store (evx_adjoint.cu)
+
+struct evx_grid {
+    int nx = 0, ny = 0, nz = 0, M = 0, Zp = 0, PZ = 0, zrows = 0;
+    evx_params p{};
+    cudaStream_t st = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    float2* S = nullptr;
+    float2* W = nullptr;
+    double* d_scal = nullptr;    // [0] cbar, [1] bulk energy, [2] gradient energy, [3..7] scratch
+    double* d_part = nullptr;
+    int npart = 0;
+    float2 *twx = nullptr, *twy = nullptr, *twz = nullptr, *rtw = nullptr;
+    float *k2x = nullptr, *k2y = nullptr, *k2z = nullptr;
+    Plan px{}, py{}, pz{};
+    bool has_field = false;
+    std::string err;
+    cudaGraphExec_t g1 = nullptr, gN = nullptr;
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;  // profiling: 5 events per recorded step
+    int ev_used = 0;                  // events of steps not yet accumulated
+    double pass_ms[4] = {0, 0, 0, 0};
+    long long pass_cnt[4] = {0, 0, 0, 0};
+    size_t bytes = 0;
+    AdjStore* adj = nullptr;
+};
+
+
+namespace evxrt {
+evx::SPassArgs y_args(const evx_grid* g, const float2* in, float2* out);
+evx::XUpdArgs x_args(const evx_grid* g, const float2* W, float2* S, float2* S_out, double dt,
+                     double M, double kappa);
+evx::ZPassArgs z_args(const evx_grid* g);
+evx_status set_error(evx_grid* g, evx_status s, const char* msg);
+void adjoint_free(evx_grid* g);  // evx_adjoint.cu
+}  // namespace evxrt

@@ -1,0 +1,101 @@
+// Internal interface between the evx runtime (C-ABI) and its CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "evx_fft.cuh"
+
+namespace evx {
+
+// Strided pass: 1D transforms along an axis whose elements are rs complex
+// apart; a tile covers P adjacent columns (kz) of one "outer" line.
+struct SPassArgs {
+    const float2* in;
+    float2* out;        // may equal in
+    int L;              // transform length
+    long long rs;       // stride between consecutive elements (complex)
+    long long os;       // stride between consecutive outer lines (complex)
+    int nouter;         // number of outer lines
+    int ncols;          // valid columns (kz = 0 .. M)
+    int nchunks;        // column chunks of P
+    Plan plan;
+    const float2* tw;   // L-entry table exp(-2 pi i m / L)
+};
+
+// x pass fused with the k-space update (one step of the scheme).
+struct XUpdArgs {
+    const float2* W;    // y,z-transformed g = c^3 - c   (F_y F_z g)
+    float2* S;          // state: F_y F_z c (without the k = 0 mode), updated in place
+    float2* S_out;      // where the new state goes (== S for a plain step)
+    int L;              // nx
+    long long rs;       // ny * Zp (stride between consecutive x)
+    long long os;       // Zp (stride between consecutive y)
+    int ny, ncols, nchunks;
+    Plan plan;
+    const float2* tw;
+    const float* k2x;   // |k_x|^2 per index (nx)
+    const float* k2y;   // (ny)
+    const float* k2z;   // (M + 1)
+    float dtM, dtMk, invL;
+};
+
+// Energy: gradient term sum_k w(kz) |k|^2 |c_hat|^2 from the state S.
+struct XEnergyArgs {
+    const float2* S;
+    int L;
+    long long rs, os;
+    int ny, ncols, nchunks, M;
+    Plan plan;
+    const float2* tw;
+    const float* k2x;
+    const float* k2y;
+    const float* k2z;
+    double* partials;   // one per CTA
+};
+
+enum ZMode { Z_STEP = 0, Z_ADJ = 1, Z_R2C = 2, Z_C2R = 3 };
+
+// z pass: real-to-complex / complex-to-real transforms of rows of nz reals
+// (half spectrum of M + 1 = nz/2 + 1 complex, row pitch Zp).
+struct ZPassArgs {
+    const float2* in;       // complex rows (Z_STEP, Z_ADJ, Z_C2R)
+    float2* out;            // complex rows (Z_STEP, Z_ADJ, Z_R2C)
+    const float* rin;       // real rows (Z_R2C)
+    float* rout;            // real rows (Z_C2R; optional side store of c in Z_STEP)
+    long long rpitch;       // floats between real rows
+    const float* cn;        // real rows of c_n (Z_ADJ)
+    long long cnpitch;
+    long long nrows;        // nx * ny
+    int M, Zp, PZ, rows_per_cta;
+    Plan plan;
+    const float2* tw;       // M-entry table exp(-2 pi i m / M)
+    const float2* rtw;      // (M + 1)-entry table exp(-2 pi i k / nz)
+    float scale;            // 1 / (ny nz)
+    const double* cbar;     // FP64 mean (Z_STEP, Z_C2R); may be null (0)
+    double* partials;       // bulk energy partial per CTA (Z_C2R) or null
+};
+
+// launchers (evx_kernels.cu)
+cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st);
+cudaError_t launch_xupdate(const XUpdArgs& a, cudaStream_t st);
+cudaError_t launch_xenergy(const XEnergyArgs& a, cudaStream_t st);
+cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st);
+int zpass_grid(const ZPassArgs& a);
+int xenergy_grid(const XEnergyArgs& a);
+// deterministic FP64 sums
+// partials[b] (b < nblocks) = FP64 sums over rows of rowlen floats, pitch floats apart
+cudaError_t launch_sum_field(const float* c, long long nrows, int rowlen, long long pitch,
+                             double* partials, int nblocks, cudaStream_t st);
+cudaError_t launch_reduce_partials(const double* partials, int n, double* out, double scale,
+                                   cudaStream_t st);
+// out = a + b (complex arrays of n elements)
+cudaError_t launch_cadd(const float2* a, const float2* b, float2* out, long long n,
+                        cudaStream_t st);
+constexpr int SUM_BLOCKS = 1216;  // 8 x 152 SMs
+
+size_t spass_smem(int L);
+size_t xupdate_smem(int L);
+size_t zpass_smem(int M, int PZ, int rows);
+
+constexpr int SP = 8;  // columns per strided tile (8 complex = 64 B contiguous)
+
+}  // namespace evx

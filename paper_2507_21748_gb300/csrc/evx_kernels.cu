@@ -1,0 +1,423 @@
+// CUDA kernels of the semi-implicit Fourier-spectral Cahn-Hilliard step
+// (paper: Appendix "Semi-implicit timestepping"; update
+//   c_hat <- (c_hat - dt M |k|^2 F{c^3 - c}) / (1 + dt M kappa |k|^4) ).
+//
+// Spectral buffers hold the half spectrum of a real nx*ny*nz field as
+// complex64 in layout [x or kx][y or ky][kz], kz = 0..M (M = nz/2) padded to
+// Zp columns. The state S holds F_y F_z c (transformed along y and z, real
+// space along x) with the k = 0 mode removed; the mean of c is carried in
+// FP64 beside it. One step is four passes over HBM:
+//   y pass inverse     S -> W
+//   z pass             W -> W : C2R along z, c = W/(ny nz) + cbar, g = c^3 - c, R2C
+//   y pass forward     W -> W       (W = F_y F_z g)
+//   x pass + update    W, S -> S : F_x both, c_hat' = a c_hat + b g_hat, F_x^-1 / nx
+// with a = 1/(1 + dt M kappa |k|^4), b = -dt M |k|^2 a.
+#include <cstdint>
+
+#include "evx_internal.h"
+
+namespace evx {
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ double block_sum_double(double v, double* ws) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) ws[warp] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (warp == 0) {
+        v = lane < nw ? ws[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;  // valid in thread 0
+}
+
+// ------------------------------------------------------------ strided pass
+// Transform SP adjacent columns (pencils) of a [L][pitch] tile along L, in
+// groups of pencils small enough for one fft_tile call.
+template <int DIR>
+__device__ __forceinline__ void fft_cols(float2* tile, int L, int pitch, const Plan& plan,
+                                         const float2* tws) {
+    const int g = max(1, min(SP, TILE_CAP / L));
+    for (int p0 = 0; p0 < SP; p0 += g) fft_tile<DIR, true>(Tile{tile + p0, L, min(g, SP - p0), pitch, 1}, plan, tws);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(NT, 2) spass_kernel(SPassArgs a) {
+    extern __shared__ float2 smem[];
+    float2* tile = smem;                 // [L][SP]
+    float2* tws = smem + a.L * SP;       // [L]
+    for (int i = threadIdx.x; i < a.L; i += NT) tws[i] = a.tw[i];
+    const int chunk = blockIdx.x, outer = blockIdx.y;
+    const long long base = (long long)outer * a.os + (long long)chunk * SP;
+    const int col0 = chunk * SP;
+    const bool full = col0 + SP <= a.ncols;
+    if (full) {
+        for (int e = threadIdx.x; e < a.L * (SP / 2); e += NT) {
+            const int i = e / (SP / 2), q = e % (SP / 2);
+            const float4 v = *reinterpret_cast<const float4*>(a.in + base + i * a.rs + 2 * q);
+            reinterpret_cast<float4*>(tile)[e] = v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < a.L * SP; e += NT) {
+            const int i = e / SP, p = e % SP;
+            tile[e] = (col0 + p < a.ncols) ? a.in[base + i * a.rs + p] : make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    fft_cols<DIR>(tile, a.L, SP, a.plan, tws);
+    if (full) {
+        for (int e = threadIdx.x; e < a.L * (SP / 2); e += NT) {
+            const int i = e / (SP / 2), q = e % (SP / 2);
+            *reinterpret_cast<float4*>(a.out + base + i * a.rs + 2 * q) =
+                reinterpret_cast<const float4*>(tile)[e];
+        }
+    } else {
+        for (int e = threadIdx.x; e < a.L * SP; e += NT) {
+            const int i = e / SP, p = e % SP;
+            if (col0 + p < a.ncols) a.out[base + i * a.rs + p] = tile[e];
+        }
+    }
+}
+
+// load SP columns of an x line into tile columns [c0, c0+SP) of a [L][2SP] tile
+__device__ __forceinline__ void load_x_cols(float2* tile, int c0, const float2* g, long long base,
+                                            long long rs, int L, int col0, int ncols) {
+    if (col0 + SP <= ncols) {
+        for (int e = threadIdx.x; e < L * (SP / 2); e += NT) {
+            const int i = e / (SP / 2), q = e % (SP / 2);
+            const float4 v = *reinterpret_cast<const float4*>(g + base + i * rs + 2 * q);
+            *reinterpret_cast<float4*>(tile + i * (2 * SP) + c0 + 2 * q) = v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < L * SP; e += NT) {
+            const int i = e / SP, p = e % SP;
+            tile[i * (2 * SP) + c0 + p] =
+                (col0 + p < ncols) ? g[base + i * rs + p] : make_float2(0.f, 0.f);
+        }
+    }
+}
+
+// ------------------------------------------------------ x pass + update
+__global__ void __launch_bounds__(NT, 1) xupdate_kernel(XUpdArgs a) {
+    extern __shared__ float2 smem[];
+    const int L = a.L;
+    float2* tile = smem;                 // [L][2 SP]: W in cols [0,SP), S in [SP, 2SP)
+    float2* tws = smem + L * 2 * SP;     // [L]
+    for (int i = threadIdx.x; i < L; i += NT) tws[i] = a.tw[i];
+    const int chunk = blockIdx.x, ky = blockIdx.y;
+    const int col0 = chunk * SP;
+    const long long base = (long long)ky * a.os + col0;
+    const bool haveW = a.W != nullptr;
+    if (haveW) load_x_cols(tile, 0, a.W, base, a.rs, L, col0, a.ncols);
+    load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols);
+    __syncthreads();
+    if (haveW) fft_cols<-1>(tile, L, 2 * SP, a.plan, tws);
+    fft_cols<-1>(tile + SP, L, 2 * SP, a.plan, tws);
+    const float k2y = a.k2y[ky];
+    for (int e = threadIdx.x; e < L * SP; e += NT) {
+        const int i = e / SP, p = e % SP;
+        const int kz = col0 + p;
+        if (kz < a.ncols) {
+            const float k2 = a.k2x[i] + k2y + a.k2z[kz];
+            const float ainv = a.invL / fmaf(a.dtMk, k2 * k2, 1.f);
+            const float b = -a.dtM * k2 * ainv;
+            const float2 c = tile[i * (2 * SP) + SP + p];
+            float2 r = make_float2(ainv * c.x, ainv * c.y);
+            if (haveW) {
+                const float2 gh = tile[i * (2 * SP) + p];
+                r.x = fmaf(b, gh.x, r.x);
+                r.y = fmaf(b, gh.y, r.y);
+            }
+            if (i == 0 && ky == 0 && kz == 0) r = make_float2(0.f, 0.f);  // mean carried in FP64
+            tile[i * (2 * SP) + SP + p] = r;
+        }
+    }
+    __syncthreads();
+    fft_cols<1>(tile + SP, L, 2 * SP, a.plan, tws);
+    if (col0 + SP <= a.ncols) {
+        for (int e = threadIdx.x; e < L * (SP / 2); e += NT) {
+            const int i = e / (SP / 2), q = e % (SP / 2);
+            *reinterpret_cast<float4*>(a.S_out + base + i * a.rs + 2 * q) =
+                *reinterpret_cast<const float4*>(tile + i * (2 * SP) + SP + 2 * q);
+        }
+    } else {
+        for (int e = threadIdx.x; e < L * SP; e += NT) {
+            const int i = e / SP, p = e % SP;
+            if (col0 + p < a.ncols) a.S_out[base + i * a.rs + p] = tile[i * (2 * SP) + SP + p];
+        }
+    }
+}
+
+// ------------------------------------------- energy: gradient term (x pass)
+__global__ void __launch_bounds__(NT, 1) xenergy_kernel(XEnergyArgs a) {
+    extern __shared__ float2 smem[];
+    __shared__ double ws[NT / 32];
+    const int L = a.L;
+    float2* tile = smem;                 // [L][2 SP], S in cols [SP, 2SP)
+    float2* tws = smem + L * 2 * SP;
+    for (int i = threadIdx.x; i < L; i += NT) tws[i] = a.tw[i];
+    const int chunk = blockIdx.x, ky = blockIdx.y;
+    const int col0 = chunk * SP;
+    const long long base = (long long)ky * a.os + col0;
+    load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols);
+    __syncthreads();
+    fft_cols<-1>(tile + SP, L, 2 * SP, a.plan, tws);
+    const double k2y = a.k2y[ky];
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < L * SP; e += NT) {
+        const int i = e / SP, p = e % SP;
+        const int kz = col0 + p;
+        if (kz < a.ncols) {
+            const double k2 = (double)a.k2x[i] + k2y + (double)a.k2z[kz];
+            const float2 c = tile[i * (2 * SP) + SP + p];
+            const double w = (kz == 0 || kz == a.M) ? 1.0 : 2.0;  // Hermitian half spectrum
+            acc += w * k2 * ((double)c.x * c.x + (double)c.y * c.y);
+        }
+    }
+    acc = block_sum_double(acc, ws);
+    if (threadIdx.x == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+// ------------------------------------------------------------- z pass
+template <int MODE>
+__global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
+    extern __shared__ float2 smem[];
+    __shared__ double ws[NT / 32];
+    const int M = a.M, PZ = a.PZ, rows = a.rows_per_cta;
+    float2* tile = smem;                  // [rows][PZ]
+    float2* tws = smem + rows * PZ;       // [M]
+    float2* rtws = tws + M;               // [M + 1]
+    for (int i = threadIdx.x; i < M; i += NT) tws[i] = a.tw[i];
+    for (int i = threadIdx.x; i <= M; i += NT) rtws[i] = a.rtw[i];
+    const long long row0 = (long long)blockIdx.x * rows;
+    const int nr = (int)min((long long)rows, a.nrows - row0);
+    const int H = M / 2 + 1;  // pairs (k, M - k), k = 0 .. M/2
+
+    if (MODE == Z_R2C) {
+        // real row of nz = 2M floats read as M complex z[n] = x[2n] + i x[2n+1]
+        for (int e = threadIdx.x; e < rows * M; e += NT) {
+            const int r = e / M, n = e - r * M;
+            tile[r * PZ + n] = r < nr ? reinterpret_cast<const float2*>(a.rin + (row0 + r) * a.rpitch)[n]
+                                      : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+    } else {
+        for (int e = threadIdx.x; e < rows * (M + 1); e += NT) {
+            const int r = e / (M + 1), i = e - r * (M + 1);
+            tile[r * PZ + i] = r < nr ? a.in[(row0 + r) * a.Zp + i] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        // C2R pre-processing: Z[k] = (X_k + conj X_{M-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{M-k});
+        // imaginary parts of X_0 and X_M are dropped (real field).
+        for (int e = threadIdx.x; e < rows * H; e += NT) {
+            const int r = e / H, k = e - r * H;
+            float2* row = tile + r * PZ;
+            if (k == 0) {
+                const float2 x0 = row[0], xm = row[M];
+                row[0] = make_float2(x0.x + xm.x, x0.x - xm.x);
+            } else {
+                const int m = M - k;
+                const float2 xk = row[k], xm = row[m];
+                const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
+                const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);
+                const float2 zk = cadd(A, mul_i<1>(cmul(cconj(rtws[k]), B)));
+                const float2 A2 = make_float2(xm.x + xk.x, xm.y - xk.y);
+                const float2 B2 = make_float2(xm.x - xk.x, xm.y + xk.y);
+                const float2 zm = cadd(A2, mul_i<1>(cmul(cconj(rtws[m]), B2)));
+                row[k] = zk;
+                if (m != k) row[m] = zm;
+            }
+        }
+        __syncthreads();
+        fft_tile<1, false>(Tile{tile, M, rows, 1, PZ}, a.plan, tws);
+        const float cb = a.cbar ? (float)(*a.cbar) : 0.f;
+        const float s = a.scale;
+        double acc = 0.0;
+        for (int e = threadIdx.x; e < nr * M; e += NT) {
+            const int r = e / M, n = e - r * M;
+            const float2 z = tile[r * PZ + n];
+            if (MODE == Z_ADJ) {
+                const float2 cn = reinterpret_cast<const float2*>(a.cn + (row0 + r) * a.cnpitch)[n];
+                const float d0 = fmaf(3.f * cn.x, cn.x, -1.f), d1 = fmaf(3.f * cn.y, cn.y, -1.f);
+                tile[r * PZ + n] = make_float2(z.x * s * d0, z.y * s * d1);
+            } else {
+                const float c0 = fmaf(z.x, s, cb), c1 = fmaf(z.y, s, cb);
+                if (MODE == Z_STEP) {
+                    if (a.rout)
+                        reinterpret_cast<float2*>(a.rout + (row0 + r) * a.rpitch)[n] = make_float2(c0, c1);
+                    tile[r * PZ + n] = make_float2(c0 * fmaf(c0, c0, -1.f), c1 * fmaf(c1, c1, -1.f));
+                } else {  // Z_C2R
+                    if (a.rout)
+                        reinterpret_cast<float2*>(a.rout + (row0 + r) * a.rpitch)[n] = make_float2(c0, c1);
+                    if (a.partials) {
+                        const double q0 = (double)c0 * c0 - 1.0, q1 = (double)c1 * c1 - 1.0;
+                        acc += q0 * q0 + q1 * q1;
+                    }
+                }
+            }
+        }
+        if (MODE == Z_C2R) {
+            if (a.partials) {
+                acc = block_sum_double(acc, ws);
+                if (threadIdx.x == 0) a.partials[blockIdx.x] = acc;
+            }
+            return;
+        }
+        __syncthreads();
+    }
+    fft_tile<-1, false>(Tile{tile, M, rows, 1, PZ}, a.plan, tws);
+    // R2C post-processing: X_k = (Z_k + conj Z_{M-k})/2 - i e^{-2 pi i k/nz} (Z_k - conj Z_{M-k})/2
+    for (int e = threadIdx.x; e < rows * H; e += NT) {
+        const int r = e / H, k = e - r * H;
+        float2* row = tile + r * PZ;
+        if (k == 0) {
+            const float2 z0 = row[0];
+            row[0] = make_float2(z0.x + z0.y, 0.f);
+            row[M] = make_float2(z0.x - z0.y, 0.f);
+        } else {
+            const int m = M - k;
+            const float2 zk = row[k], zm = row[m];
+            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
+            const float2 xk = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
+            const float2 A2 = make_float2(0.5f * (zm.x + zk.x), 0.5f * (zm.y - zk.y));
+            const float2 B2 = make_float2(0.5f * (zm.x - zk.x), 0.5f * (zm.y + zk.y));
+            const float2 xm = cadd(A2, mul_i<-1>(cmul(rtws[m], B2)));
+            row[k] = xk;
+            if (m != k) row[m] = xm;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * (M + 1); e += NT) {
+        const int r = e / (M + 1), i = e - r * (M + 1);
+        a.out[(row0 + r) * a.Zp + i] = tile[r * PZ + i];
+    }
+}
+
+// --------------------------------------------------- FP64 sums of a field
+// partials[b] = sum over rows b, b + nblocks, ... of sum_z c[row * pitch + z]
+__global__ void __launch_bounds__(NT) sum_rows_kernel(const float* c, long long nrows, int rowlen,
+                                                      long long pitch, double* partials) {
+    __shared__ double ws[NT / 32];
+    double acc = 0.0;
+    for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const float* row = c + r * pitch;
+        for (int z = threadIdx.x; z < rowlen; z += NT) acc += (double)row[z];
+    }
+    acc = block_sum_double(acc, ws);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(1024) reduce_partials_kernel(const double* partials, int n,
+                                                                double* out, double scale) {
+    __shared__ double ws[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) acc += partials[i];
+    acc = block_sum_double(acc, ws);
+    if (threadIdx.x == 0) *out = acc * scale;
+}
+
+__global__ void cadd_kernel(const float2* a, const float2* b, float2* out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = cadd(a[i], b[i]);
+}
+
+// ------------------------------------------------------------- launchers
+size_t spass_smem(int L) { return sizeof(float2) * ((size_t)L * SP + L); }
+size_t xupdate_smem(int L) { return sizeof(float2) * ((size_t)L * 2 * SP + L); }
+size_t zpass_smem(int M, int PZ, int rows) {
+    return sizeof(float2) * ((size_t)rows * PZ + M + M + 1);
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st) {
+    const size_t sm = spass_smem(a.L);
+    dim3 grid(a.nchunks, a.nouter);
+    cudaError_t e;
+    if (dir < 0) {
+        if ((e = set_smem(spass_kernel<-1>, sm)) != cudaSuccess) return e;
+        spass_kernel<-1><<<grid, NT, sm, st>>>(a);
+    } else {
+        if ((e = set_smem(spass_kernel<1>, sm)) != cudaSuccess) return e;
+        spass_kernel<1><<<grid, NT, sm, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xupdate(const XUpdArgs& a, cudaStream_t st) {
+    const size_t sm = xupdate_smem(a.L);
+    cudaError_t e;
+    if ((e = set_smem(xupdate_kernel, sm)) != cudaSuccess) return e;
+    xupdate_kernel<<<dim3(a.nchunks, a.ny), NT, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+int xenergy_grid(const XEnergyArgs& a) { return a.nchunks * a.ny; }
+
+cudaError_t launch_xenergy(const XEnergyArgs& a, cudaStream_t st) {
+    const size_t sm = xupdate_smem(a.L);
+    cudaError_t e;
+    if ((e = set_smem(xenergy_kernel, sm)) != cudaSuccess) return e;
+    xenergy_kernel<<<dim3(a.nchunks, a.ny), NT, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+int zpass_grid(const ZPassArgs& a) {
+    return (int)((a.nrows + a.rows_per_cta - 1) / a.rows_per_cta);
+}
+
+cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st) {
+    const size_t sm = zpass_smem(a.M, a.PZ, a.rows_per_cta);
+    const int grid = zpass_grid(a);
+    cudaError_t e = cudaSuccess;
+    switch (mode) {
+        case Z_STEP:
+            if ((e = set_smem(zpass_kernel<Z_STEP>, sm)) != cudaSuccess) return e;
+            zpass_kernel<Z_STEP><<<grid, NT, sm, st>>>(a);
+            break;
+        case Z_ADJ:
+            if ((e = set_smem(zpass_kernel<Z_ADJ>, sm)) != cudaSuccess) return e;
+            zpass_kernel<Z_ADJ><<<grid, NT, sm, st>>>(a);
+            break;
+        case Z_R2C:
+            if ((e = set_smem(zpass_kernel<Z_R2C>, sm)) != cudaSuccess) return e;
+            zpass_kernel<Z_R2C><<<grid, NT, sm, st>>>(a);
+            break;
+        case Z_C2R:
+            if ((e = set_smem(zpass_kernel<Z_C2R>, sm)) != cudaSuccess) return e;
+            zpass_kernel<Z_C2R><<<grid, NT, sm, st>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_field(const float* c, long long nrows, int rowlen, long long pitch,
+                             double* partials, int nblocks, cudaStream_t st) {
+    sum_rows_kernel<<<nblocks, NT, 0, st>>>(c, nrows, rowlen, pitch, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double* partials, int n, double* out, double scale,
+                                   cudaStream_t st) {
+    reduce_partials_kernel<<<1, 1024, 0, st>>>(partials, n, out, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cadd(const float2* a, const float2* b, float2* out, long long n,
+                        cudaStream_t st) {
+    cadd_kernel<<<SUM_BLOCKS, NT, 0, st>>>(a, b, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace evx

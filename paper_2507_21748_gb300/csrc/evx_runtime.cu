@@ -1,0 +1,549 @@
+// Host runtime of the evx C-ABI (include/evx.h): grid plans, tables,
+// buffers, pass sequencing, CUDA graphs and error state.
+#include <cmath>
+#include <cstdint>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "evx_grid_impl.h"
+
+using namespace evx;
+
+static const int GRAPH_CHUNK = 16;
+static thread_local std::string tl_err;
+
+static evx_status fail(evx_grid* g, evx_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (g) g->err = buf;
+    tl_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(g, EVX_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static bool smooth235(int n) {
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+static Plan make_plan(int L) {
+    Plan pl{};
+    int n = L;
+    while (n % 5 == 0) { pl.r[pl.n++] = 5; n /= 5; }
+    while (n % 3 == 0) { pl.r[pl.n++] = 3; n /= 3; }
+    while (n % 16 == 0) { pl.r[pl.n++] = 16; n /= 16; }
+    if (n == 8 || n == 4 || n == 2) { pl.r[pl.n++] = n; n = 1; }
+    return pl;
+}
+
+static std::vector<float2> twiddles(int L) {
+    std::vector<float2> t(L);
+    for (int m = 0; m < L; ++m) {
+        const double ang = -2.0 * M_PI * (double)m / (double)L;
+        t[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    return t;
+}
+
+static std::vector<float> k2table(int n, double h, int count) {
+    std::vector<float> t(count);
+    for (int m = 0; m < count; ++m) {
+        const int ms = m <= n / 2 ? m : m - n;
+        const double k = 2.0 * M_PI * (double)ms / ((double)n * h);
+        t[m] = (float)(k * k);
+    }
+    return t;
+}
+
+static evx_status check_params(evx_grid* g, const evx_params& p) {
+    if (!(p.dt >= 0) || !(p.M >= 0) || !(p.kappa >= 0) || !(p.h > 0) || !std::isfinite(p.dt) ||
+        !std::isfinite(p.M) || !std::isfinite(p.kappa) || !std::isfinite(p.h))
+        return fail(g, EVX_ERR_ARG, "invalid parameters dt=%g M=%g kappa=%g h=%g", p.dt, p.M,
+                    p.kappa, p.h);
+    return EVX_OK;
+}
+
+static void drop_graphs(evx_grid* g) {
+    if (g->g1) cudaGraphExecDestroy(g->g1);
+    if (g->gN) cudaGraphExecDestroy(g->gN);
+    g->g1 = g->gN = nullptr;
+}
+
+template <typename T>
+static evx_status dmalloc(evx_grid* g, T** ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(g, EVX_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    g->bytes += bytes;
+    return EVX_OK;
+}
+
+template <typename T>
+static evx_status upload(evx_grid* g, T** ptr, const std::vector<T>& v) {
+    evx_status s = dmalloc(g, ptr, sizeof(T) * v.size());
+    if (s != EVX_OK) return s;
+    CK(cudaMemcpy(*ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return EVX_OK;
+}
+
+static evx_status upload_k2(evx_grid* g) {
+    std::vector<float> kx = k2table(g->nx, g->p.h, g->nx), ky = k2table(g->ny, g->p.h, g->ny),
+                       kz = k2table(g->nz, g->p.h, g->M + 1);
+    CK(cudaMemcpy(g->k2x, kx.data(), sizeof(float) * kx.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(g->k2y, ky.data(), sizeof(float) * ky.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(g->k2z, kz.data(), sizeof(float) * kz.size(), cudaMemcpyHostToDevice));
+    return EVX_OK;
+}
+
+// ------------------------------------------------------------ pass args
+namespace evxrt {
+
+SPassArgs y_args(const evx_grid* g, const float2* in, float2* out) {
+    SPassArgs a{};
+    a.in = in;
+    a.out = out;
+    a.L = g->ny;
+    a.rs = g->Zp;
+    a.os = (long long)g->ny * g->Zp;
+    a.nouter = g->nx;
+    a.ncols = g->M + 1;
+    a.nchunks = g->Zp / SP;
+    a.plan = g->py;
+    a.tw = g->twy;
+    return a;
+}
+
+XUpdArgs x_args(const evx_grid* g, const float2* W, float2* S, float2* S_out, double dt, double M,
+                double kappa) {
+    XUpdArgs a{};
+    a.W = W;
+    a.S = S;
+    a.S_out = S_out;
+    a.L = g->nx;
+    a.rs = (long long)g->ny * g->Zp;
+    a.os = g->Zp;
+    a.ny = g->ny;
+    a.ncols = g->M + 1;
+    a.nchunks = g->Zp / SP;
+    a.plan = g->px;
+    a.tw = g->twx;
+    a.k2x = g->k2x;
+    a.k2y = g->k2y;
+    a.k2z = g->k2z;
+    a.dtM = (float)(dt * M);
+    a.dtMk = (float)(dt * M * kappa);
+    a.invL = (float)(1.0 / g->nx);
+    return a;
+}
+
+ZPassArgs z_args(const evx_grid* g) {
+    ZPassArgs a{};
+    a.nrows = (long long)g->nx * g->ny;
+    a.M = g->M;
+    a.Zp = g->Zp;
+    a.PZ = g->PZ;
+    a.rows_per_cta = g->zrows;
+    a.plan = g->pz;
+    a.tw = g->twz;
+    a.rtw = g->rtw;
+    a.scale = (float)(1.0 / ((double)g->ny * g->nz));
+    return a;
+}
+
+evx_status set_error(evx_grid* g, evx_status s, const char* msg) { return fail(g, s, "%s", msg); }
+
+}  // namespace evxrt
+using namespace evxrt;
+
+// --------------------------------------------------------- step sequence
+// ev: null, or 5 events recorded around the four passes
+static cudaError_t issue_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) {
+    cudaError_t e;
+    if (ev) cudaEventRecord(ev[0], st);
+    if ((e = launch_spass(y_args(g, g->S, g->W), +1, st)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
+    ZPassArgs z = z_args(g);
+    z.in = g->W;
+    z.out = g->W;
+    z.cbar = g->d_scal;
+    if ((e = launch_zpass(z, Z_STEP, st)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], st);
+    if ((e = launch_spass(y_args(g, g->W, g->W), -1, st)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], st);
+    if ((e = launch_xupdate(x_args(g, g->W, g->S, g->S, g->p.dt, g->p.M, g->p.kappa), st)) !=
+        cudaSuccess)
+        return e;
+    if (ev) cudaEventRecord(ev[4], st);
+    return cudaSuccess;
+}
+
+// add the recorded event intervals to the per-pass totals (synchronises)
+static evx_status drain_events(evx_grid* g) {
+    if (g->ev_used == 0) return EVX_OK;
+    CK(cudaEventSynchronize(g->evpool[g->ev_used - 1]));
+    for (int s = 0; s < g->ev_used; s += 5) {
+        float ms[4];
+        for (int k = 0; k < 4; ++k)
+            CK(cudaEventElapsedTime(&ms[k], g->evpool[s + k], g->evpool[s + k + 1]));
+        // event order: y inverse, z, y forward, x + update  ->  pass ids 1, 2, 3, 0
+        g->pass_ms[1] += ms[0];
+        g->pass_ms[2] += ms[1];
+        g->pass_ms[3] += ms[2];
+        g->pass_ms[0] += ms[3];
+        for (int k = 0; k < 4; ++k) g->pass_cnt[k] += 1;
+    }
+    g->ev_used = 0;
+    return EVX_OK;
+}
+
+static evx_status build_graph(evx_grid* g, int nsteps, cudaGraphExec_t* out) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nsteps && e == cudaSuccess; ++i) e = issue_step(g, g->cap, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(g->cap, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(g, EVX_ERR_CUDA, "graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(g, EVX_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return EVX_OK;
+}
+
+// ================================================================ C-ABI
+extern "C" {
+
+const char* evx_last_error(const evx_grid* g) { return g ? g->err.c_str() : tl_err.c_str(); }
+
+evx_status evx_grid_destroy(evx_grid* g);
+
+evx_status evx_grid_create(int nx, int ny, int nz, evx_params p, void* cuda_stream, evx_grid** out) {
+    evx_grid* g = nullptr;
+    if (!out) return fail(g, EVX_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    const int dims[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+        const int n = dims[d];
+        if (n < 8 || n > 1024 || (n & 1) || !smooth235(n))
+            return fail(g, EVX_ERR_SIZE,
+                        "grid size %d x %d x %d unsupported: each edge must be even, 8..1024, "
+                        "with prime factors 2, 3, 5 only",
+                        nx, ny, nz);
+    }
+    if (check_params(nullptr, p) != EVX_OK) return EVX_ERR_ARG;
+    g = new evx_grid();
+    g->nx = nx;
+    g->ny = ny;
+    g->nz = nz;
+    g->M = nz / 2;
+    g->Zp = ((g->M + 1 + SP - 1) / SP) * SP;
+    g->PZ = (g->M + 2) & ~1;
+    g->zrows = TILE_CAP / g->PZ;
+    if (g->zrows < 1) g->zrows = 1;
+    g->p = p;
+    g->st = (cudaStream_t)cuda_stream;
+    g->px = make_plan(nx);
+    g->py = make_plan(ny);
+    g->pz = make_plan(g->M);
+    evx_status s;
+    const size_t nspec = (size_t)nx * ny * g->Zp;
+#define TRY(x)                       \
+    do {                             \
+        s = (x);                     \
+        if (s != EVX_OK) goto bad;   \
+    } while (0)
+    {
+        TRY(dmalloc(g, &g->S, nspec * sizeof(float2)));
+        TRY(dmalloc(g, &g->W, nspec * sizeof(float2)));
+        TRY(dmalloc(g, &g->d_scal, 8 * sizeof(double)));
+        ZPassArgs z = z_args(g);
+        const int zg = zpass_grid(z);
+        const int xg = (g->Zp / SP) * ny;
+        g->npart = std::max(std::max(zg, xg), SUM_BLOCKS);
+        TRY(dmalloc(g, &g->d_part, (size_t)g->npart * sizeof(double)));
+        TRY(upload(g, &g->twx, twiddles(nx)));
+        TRY(upload(g, &g->twy, twiddles(ny)));
+        TRY(upload(g, &g->twz, twiddles(g->M)));
+        {
+            std::vector<float2> r(g->M + 1);
+            for (int k = 0; k <= g->M; ++k) {
+                const double ang = -2.0 * M_PI * (double)k / (double)nz;
+                r[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            }
+            TRY(upload(g, &g->rtw, r));
+        }
+        TRY(dmalloc(g, &g->k2x, sizeof(float) * nx));
+        TRY(dmalloc(g, &g->k2y, sizeof(float) * ny));
+        TRY(dmalloc(g, &g->k2z, sizeof(float) * (g->M + 1)));
+        TRY(upload_k2(g));
+        cudaError_t e = cudaMemset(g->d_scal, 0, 8 * sizeof(double));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            s = fail(g, EVX_ERR_CUDA, "create: %s", cudaGetErrorString(e));
+            goto bad;
+        }
+    }
+#undef TRY
+    *out = g;
+    return EVX_OK;
+bad:
+    tl_err = g->err;
+    evx_grid_destroy(g);
+    return s;
+}
+
+evx_status evx_grid_destroy(evx_grid* g) {
+    if (!g) return EVX_OK;
+    if (g->st || g->S) cudaStreamSynchronize(g->st);
+    evxrt::adjoint_free(g);
+    drop_graphs(g);
+    for (auto ptr : {(void*)g->S, (void*)g->W, (void*)g->d_scal, (void*)g->d_part, (void*)g->twx,
+                     (void*)g->twy, (void*)g->twz, (void*)g->rtw, (void*)g->k2x, (void*)g->k2y,
+                     (void*)g->k2z})
+        if (ptr) cudaFree(ptr);
+    for (auto e : g->evpool) cudaEventDestroy(e);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    delete g;
+    return EVX_OK;
+}
+
+evx_status evx_set_params(evx_grid* g, evx_params p) {
+    if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
+    if (check_params(g, p) != EVX_OK) return EVX_ERR_ARG;
+    const bool hchg = p.h != g->p.h;
+    g->p = p;
+    drop_graphs(g);
+    if (hchg) {
+        CK(cudaStreamSynchronize(g->st));
+        return upload_k2(g);
+    }
+    return EVX_OK;
+}
+
+evx_status evx_set_stream(evx_grid* g, void* cuda_stream) {
+    if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
+    g->st = (cudaStream_t)cuda_stream;
+    return EVX_OK;
+}
+
+static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+// real rows (pitch floats apart) -> spectral state S, FP64 mean -> d_scal[0]
+static evx_status load_real(evx_grid* g, const float* rows, long long pitch) {
+    const long long nrows = (long long)g->nx * g->ny;
+    const double V = (double)nrows * g->nz;
+    CK(launch_sum_field(rows, nrows, g->nz, pitch, g->d_part, SUM_BLOCKS, g->st));
+    CK(launch_reduce_partials(g->d_part, SUM_BLOCKS, g->d_scal + 0, 1.0 / V, g->st));
+    ZPassArgs z = z_args(g);
+    z.rin = rows;
+    z.rpitch = pitch;
+    z.out = g->W;
+    CK(launch_zpass(z, Z_R2C, g->st));
+    CK(launch_spass(y_args(g, g->W, g->W), -1, g->st));
+    // x pass with a = 1, b = 0: removes the k = 0 mode (carried in FP64)
+    CK(launch_xupdate(x_args(g, nullptr, g->W, g->S, 0.0, 0.0, 0.0), g->st));
+    g->has_field = true;
+    return EVX_OK;
+}
+
+evx_status evx_set_field(evx_grid* g, const float* d_c) {
+    if (!g || !d_c) return fail(g, EVX_ERR_ARG, "NULL argument");
+    if (!aligned8(d_c)) return fail(g, EVX_ERR_ARG, "field pointer must be 8-byte aligned");
+    return load_real(g, d_c, g->nz);
+}
+
+evx_status evx_set_field_host(evx_grid* g, const float* h_c) {
+    if (!g || !h_c) return fail(g, EVX_ERR_ARG, "NULL argument");
+    // stage real rows into the work buffer's row slots (pitch 2 Zp floats), then R2C in place
+    const long long nrows = (long long)g->nx * g->ny;
+    CK(cudaMemcpy2DAsync(g->W, sizeof(float) * 2 * g->Zp, h_c, sizeof(float) * g->nz,
+                         sizeof(float) * g->nz, nrows, cudaMemcpyHostToDevice, g->st));
+    evx_status s = load_real(g, (const float*)g->W, 2LL * g->Zp);
+    if (s != EVX_OK) return s;
+    CK(cudaStreamSynchronize(g->st));
+    return EVX_OK;
+}
+
+// state -> real rows (pitch floats apart), optional bulk-energy partials
+static evx_status store_real(evx_grid* g, float* rows, long long pitch, double* partials) {
+    CK(launch_spass(y_args(g, g->S, g->W), +1, g->st));
+    ZPassArgs z = z_args(g);
+    z.in = g->W;
+    z.rout = rows;
+    z.rpitch = pitch;
+    z.cbar = g->d_scal;
+    z.partials = partials;
+    CK(launch_zpass(z, Z_C2R, g->st));
+    return EVX_OK;
+}
+
+evx_status evx_get_field(evx_grid* g, float* d_out) {
+    if (!g || !d_out) return fail(g, EVX_ERR_ARG, "NULL argument");
+    if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    if (!aligned8(d_out)) return fail(g, EVX_ERR_ARG, "output pointer must be 8-byte aligned");
+    return store_real(g, d_out, g->nz, nullptr);
+}
+
+evx_status evx_get_field_host(evx_grid* g, float* h_out) {
+    if (!g || !h_out) return fail(g, EVX_ERR_ARG, "NULL argument");
+    if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, nullptr);
+    if (s != EVX_OK) return s;
+    const long long nrows = (long long)g->nx * g->ny;
+    CK(cudaMemcpy2DAsync(h_out, sizeof(float) * g->nz, g->W, sizeof(float) * 2 * g->Zp,
+                         sizeof(float) * g->nz, nrows, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return EVX_OK;
+}
+
+evx_status evx_ch_step(evx_grid* g, int n_steps) {
+    if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
+    if (n_steps < 0) return fail(g, EVX_ERR_ARG, "n_steps < 0");
+    if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    if (n_steps == 0) return EVX_OK;
+    if (g->prof) {
+        for (int i = 0; i < n_steps; ++i) {
+            if ((size_t)g->ev_used + 5 > g->evpool.size()) {
+                if (g->evpool.size() >= 5 * 4096) {
+                    evx_status s = drain_events(g);
+                    if (s != EVX_OK) return s;
+                } else {
+                    for (int k = 0; k < 5; ++k) {
+                        cudaEvent_t e;
+                        CK(cudaEventCreate(&e));
+                        g->evpool.push_back(e);
+                    }
+                }
+            }
+            CK(issue_step(g, g->st, &g->evpool[g->ev_used]));
+            g->ev_used += 5;
+        }
+        return EVX_OK;
+    }
+    if (!g->g1) {
+        evx_status s = build_graph(g, 1, &g->g1);
+        if (s != EVX_OK) return s;
+    }
+    if (n_steps >= GRAPH_CHUNK && !g->gN) {
+        evx_status s = build_graph(g, GRAPH_CHUNK, &g->gN);
+        if (s != EVX_OK) return s;
+    }
+    int left = n_steps;
+    while (left >= GRAPH_CHUNK) {
+        CK(cudaGraphLaunch(g->gN, g->st));
+        left -= GRAPH_CHUNK;
+    }
+    while (left-- > 0) CK(cudaGraphLaunch(g->g1, g->st));
+    return EVX_OK;
+}
+
+evx_status evx_energy(evx_grid* g, double* E, double* mass) {
+    if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
+    if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    const double h3 = g->p.h * g->p.h * g->p.h;
+    const double V = (double)g->nx * g->ny * g->nz;
+    // bulk: h^3/4 sum (c^2-1)^2 over the real field (written into W's row slots, discarded)
+    evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, g->d_part);
+    if (s != EVX_OK) return s;
+    ZPassArgs z = z_args(g);
+    CK(launch_reduce_partials(g->d_part, zpass_grid(z), g->d_scal + 1, 0.25 * h3, g->st));
+    // gradient: h^3 (kappa/2)(1/V) sum_k |k|^2 |c_hat|^2
+    XEnergyArgs xa{};
+    xa.S = g->S;
+    xa.L = g->nx;
+    xa.rs = (long long)g->ny * g->Zp;
+    xa.os = g->Zp;
+    xa.ny = g->ny;
+    xa.ncols = g->M + 1;
+    xa.nchunks = g->Zp / SP;
+    xa.M = g->M;
+    xa.plan = g->px;
+    xa.tw = g->twx;
+    xa.k2x = g->k2x;
+    xa.k2y = g->k2y;
+    xa.k2z = g->k2z;
+    xa.partials = g->d_part;
+    CK(launch_xenergy(xa, g->st));
+    CK(launch_reduce_partials(g->d_part, xenergy_grid(xa), g->d_scal + 2,
+                              0.5 * g->p.kappa * h3 / V, g->st));
+    double host[3];
+    CK(cudaMemcpyAsync(host, g->d_scal, sizeof host, cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    const double e = host[1] + host[2];
+    if (!std::isfinite(e) || !std::isfinite(host[0]))
+        return fail(g, EVX_ERR_NONFINITE, "field holds NaN or Inf (energy %g, mean %g)", e, host[0]);
+    if (E) *E = e;
+    if (mass) *mass = h3 * V * host[0];
+    return EVX_OK;
+}
+
+evx_status evx_mean(evx_grid* g, double* cbar) {
+    if (!g || !cbar) return fail(g, EVX_ERR_ARG, "NULL argument");
+    if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    CK(cudaMemcpyAsync(cbar, g->d_scal, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+    CK(cudaStreamSynchronize(g->st));
+    return EVX_OK;
+}
+
+evx_status evx_footprint(const evx_grid* g, size_t* bytes) {
+    if (!g || !bytes) return fail(nullptr, EVX_ERR_ARG, "NULL argument");
+    *bytes = g->bytes;
+    return EVX_OK;
+}
+
+evx_status evx_set_profiling(evx_grid* g, int on) {
+    if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
+    if (!on) {
+        evx_status s = drain_events(g);
+        if (s != EVX_OK) return s;
+    }
+    g->prof = on != 0;
+    return EVX_OK;
+}
+
+evx_status evx_pass_times(evx_grid* g, double* ms, long long* counts, int reset) {
+    if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
+    CK(cudaStreamSynchronize(g->st));
+    evx_status s = drain_events(g);
+    if (s != EVX_OK) return s;
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = g->pass_ms[k];
+        if (counts) counts[k] = g->pass_cnt[k];
+        if (reset) {
+            g->pass_ms[k] = 0;
+            g->pass_cnt[k] = 0;
+        }
+    }
+    return EVX_OK;
+}
+
+evx_status evx_pass_bytes(const evx_grid* g, int pass, double* bytes) {
+    if (!g || !bytes || pass < 0 || pass > 3) return fail(nullptr, EVX_ERR_ARG, "bad argument");
+    // one half-spectrum field: nx * ny * (M + 1) complex64 elements
+    const double F = (double)g->nx * g->ny * (g->M + 1) * sizeof(float2);
+    // pass 0 reads W and S, writes S; passes 1..3 read one field and write one
+    *bytes = pass == 0 ? 3.0 * F : 2.0 * F;
+    return EVX_OK;
+}
+
+}  // extern "C"
+

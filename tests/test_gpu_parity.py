@@ -1,0 +1,202 @@
+"""GPU parity of the CUDA Cahn-Hilliard step against the FP64 oracle.
+
+Bars (from the method's stated accuracy targets): relative L2 <= 1e-5 after
+one step and <= 1e-3 after 100 steps, FP32 bulk against the FP64 oracle, on
+the same seeded FP32 inputs; the FP64 mean is carried exactly.
+All calls go through the C-ABI (ctypes binding); nothing here runs on a CPU
+fallback.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2507_21748_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DT, M, KAPPA, H = 0.1, 1.0, 1.0, 1.0
+
+
+@pytest.fixture(scope="module")
+def evx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_21748_gb300 import evx as E
+    return E
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_run(evx, c0, nsteps, **params):
+    import torch
+    p = dict(dt=DT, M=M, kappa=KAPPA, h=H)
+    p.update(params)
+    g = evx.Grid(c0.shape, **p)
+    g.set_field(torch.from_numpy(c0).cuda())
+    g.step(nsteps)
+    out = g.get_field().cpu().numpy()
+    g.close()
+    return out
+
+
+# sizes that span several tiles, ragged column chunks and radix 3 / 5 stages
+SMALL = [(8, 8, 8), (16, 32, 64), (48, 40, 36), (24, 30, 50), (64, 64, 64)]
+
+
+@pytest.mark.parametrize("shape", SMALL + [(400, 16, 20), (10, 1024, 12)])
+def test_roundtrip(evx, shape):
+    import torch
+    c = inputs.uniform_field(shape, seed=3, offset=0.3)
+    g = evx.Grid(shape)
+    g.set_field(torch.from_numpy(c).cuda())
+    back = g.get_field().cpu().numpy()
+    mean = g.mean()
+    g.close()
+    assert np.abs(back - c).max() < 2e-6
+    assert abs(mean - c.astype(np.float64).mean()) < 1e-15
+
+
+@pytest.mark.parametrize("shape", SMALL + [(128, 128, 128)])
+def test_one_step_vs_oracle(evx, shape):
+    c0 = inputs.uniform_field(shape, seed=0)
+    ref = O.ch_step(c0, DT, M, KAPPA, H, 1)
+    got = gpu_run(evx, c0, 1)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (48, 40, 36), (128, 128, 128)])
+def test_100_steps_vs_oracle(evx, shape):
+    c0 = inputs.uniform_field(shape, seed=0)
+    ref = O.ch_step(c0, DT, M, KAPPA, H, 100, check_imag=False)
+    got = gpu_run(evx, c0, 100)
+    assert rel_l2(got, ref) <= 1e-3
+
+
+@pytest.mark.parametrize("offset", [0.0, 0.3])
+def test_parameters_and_offset(evx, offset):
+    shape = (32, 40, 48)
+    c0 = inputs.uniform_field(shape, seed=9, offset=offset, lo=-0.3, hi=0.3)
+    ref = O.ch_step(c0, 0.05, 0.7, 1.6, 0.8, 5)
+    got = gpu_run(evx, c0, 5, dt=0.05, M=0.7, kappa=1.6, h=0.8)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("n,plane", [(256, "xy"), (400, "xz")])
+def test_100_steps_reduced_dimension(evx, n, plane):
+    """A field constant along one axis evolves as the 2D problem; the oracle
+    runs that 2D problem exactly and the whole 3D GPU field must match it."""
+    shape2 = {"xy": (n, n, 1), "xz": (n, 1, n), "yz": (1, n, n)}[plane]
+    c2 = inputs.uniform_field(shape2, seed=4)
+    ref = O.ch_step(c2, DT, M, KAPPA, H, 100, check_imag=False)
+    c3 = np.ascontiguousarray(np.broadcast_to(c2, (n, n, n)))
+    got = gpu_run(evx, c3, 100)
+    assert rel_l2(got, np.broadcast_to(ref, (n, n, n))) <= 1e-3
+
+
+def test_one_step_400_cubed(evx):
+    shape = (400, 400, 400)
+    c0 = inputs.uniform_field(shape, seed=0)
+    ref = O.ch_step(c0, DT, M, KAPPA, H, 1, check_imag=False)
+    got = gpu_run(evx, c0, 1)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_mass_and_energy_trace(evx):
+    import torch
+    shape = (64, 64, 64)
+    c0 = inputs.uniform_field(shape, seed=0)
+    _, E_ref = O.ch_step(c0, DT, M, KAPPA, H, 100, energies=True, check_imag=False)
+    g = evx.Grid(shape)
+    g.set_field(torch.from_numpy(c0).cuda())
+    mean0 = g.mean()
+    Es = []
+    for k in range(11):
+        if k:
+            g.step(10)
+        E, mass = g.energy()
+        Es.append(E)
+        assert mass == mean0 * 64 ** 3  # FP64 mean carried exactly
+    cN = g.get_field().cpu().numpy().astype(np.float64)
+    g.close()
+    Es = np.array(Es)
+    assert np.all(np.diff(Es) < 0)
+    assert np.abs(Es - E_ref[::10]).max() / np.abs(E_ref).max() < 1e-5
+    # FP64 sum of the FP32 real field: drift bounded by FP32 rounding of the field
+    l1 = np.abs(c0.astype(np.float64)).sum()
+    assert abs(cN.sum() - c0.astype(np.float64).sum()) / l1 < 1e-6
+
+
+def test_graph_and_profiled_paths_identical(evx):
+    import torch
+    shape = (48, 40, 36)
+    c0 = torch.from_numpy(inputs.uniform_field(shape, seed=2)).cuda()
+    outs = []
+    for prof in (False, True):
+        g = evx.Grid(shape)
+        g.set_profiling(prof)
+        g.set_field(c0)
+        g.step(37)
+        outs.append(g.get_field().cpu())
+        if prof:
+            ms, cnt = g.pass_times()
+            assert cnt == [37, 37, 37, 37]
+            assert all(m > 0 for m in ms)
+        g.close()
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_host_io_matches_device_io(evx):
+    import torch
+    shape = (32, 48, 40)
+    c0 = inputs.uniform_field(shape, seed=5, offset=0.1)
+    g = evx.Grid(shape)
+    g.set_field_host(torch.from_numpy(c0))
+    g.step(3)
+    a = g.get_field_host().clone()
+    b = g.get_field().cpu()
+    g2 = evx.Grid(shape)
+    g2.set_field(torch.from_numpy(c0).cuda())
+    g2.step(3)
+    c = g2.get_field().cpu()
+    g.close()
+    g2.close()
+    assert torch.equal(a, b)
+    assert torch.equal(a, c)
+
+
+def test_nonfinite_detected(evx):
+    import torch
+    shape = (16, 16, 16)
+    c0 = inputs.uniform_field(shape, seed=1)
+    c0[3, 4, 5] = np.nan
+    g = evx.Grid(shape)
+    g.set_field(torch.from_numpy(c0).cuda())
+    with pytest.raises(evx.EvxError) as ei:
+        g.energy()
+    assert ei.value.status == evx.EVX_ERR_NONFINITE
+    g.close()
+
+
+def test_state_errors(evx):
+    g = evx.Grid((8, 8, 8))
+    with pytest.raises(evx.EvxError) as ei:
+        g.step(1)
+    assert ei.value.status == evx.EVX_ERR_STATE
+    with pytest.raises(evx.EvxError):
+        g.energy()
+    g.close()
+
+
+def test_zero_mobility_identity_and_constant_fixed_point(evx):
+    shape = (16, 24, 20)
+    c0 = inputs.uniform_field(shape, seed=6, lo=-0.8, hi=0.8)
+    got = gpu_run(evx, c0, 5, M=0.0)
+    assert np.abs(got - c0).max() < 2e-6
+    cc = np.full(shape, 0.37, dtype=np.float32)
+    got = gpu_run(evx, cc, 5)
+    assert np.abs(got - cc).max() < 1e-6

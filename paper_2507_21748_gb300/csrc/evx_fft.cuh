@@ -145,6 +145,57 @@ struct Dft<16, DIR> {
         t = v[11]; v[11] = v[14]; v[14] = t;
     }
 };
+// multiply by exp(DIR * i pi m / 16) for fixed m < 16 (32nd roots of unity)
+template <int DIR, int m>
+__device__ __forceinline__ float2 w32(float2 a) {
+    // cos(pi j / 16), j = 0..8
+    constexpr float C[9] = {1.0f,
+                            0.98078528040323043f,
+                            0.92387953251128674f,
+                            0.83146961230254524f,
+                            0.70710678118654752f,
+                            0.55557023301960218f,
+                            0.38268343236508978f,
+                            0.19509032201612825f,
+                            0.0f};
+    if (m == 0) return a;
+    if (m == 8) return mul_i<DIR>(a);
+    // exp(-i pi m/16) = cos - i sin; for m > 8: cos(pi m/16) = -cos(pi (16-m)/16)
+    constexpr float c = m <= 8 ? C[m] : -C[16 - m];
+    constexpr float s = m <= 8 ? C[8 - m] : C[m - 8];
+    const float ds = DIR < 0 ? -s : s;
+    return make_float2(fmaf(a.x, c, -a.y * ds), fmaf(a.x, ds, a.y * c));
+}
+
+template <int DIR>
+struct Dft<32, DIR> {
+    // decimation in time: E = DFT16(even), O = DFT16(odd), X_k = E_k + w32^k O_k
+    template <int k>
+    __device__ __forceinline__ static void comb(float2* v, float2* e, float2* o) {
+        const float2 t = w32<DIR, k>(o[k]);
+        v[k] = cadd(e[k], t);
+        v[k + 16] = csub(e[k], t);
+    }
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 e[16], o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        Dft<16, DIR>::run(e);
+        Dft<16, DIR>::run(o);
+        comb<0>(v, e, o);  comb<1>(v, e, o);  comb<2>(v, e, o);  comb<3>(v, e, o);
+        comb<4>(v, e, o);  comb<5>(v, e, o);  comb<6>(v, e, o);  comb<7>(v, e, o);
+        comb<8>(v, e, o);  comb<9>(v, e, o);  comb<10>(v, e, o); comb<11>(v, e, o);
+        comb<12>(v, e, o); comb<13>(v, e, o); comb<14>(v, e, o); comb<15>(v, e, o);
+    }
+};
+template <int DIR>
+struct Dft<1, DIR> {
+    __device__ __forceinline__ static void run(float2*) {}
+};
+
 template <int DIR>
 struct Dft<3, DIR> {
     __device__ __forceinline__ static void run(float2* v) {

@@ -92,6 +92,12 @@ cudaError_t launch_cadd(const float2* a, const float2* b, float2* out, long long
                         cudaStream_t st);
 constexpr int SUM_BLOCKS = 1216;  // 8 x 152 SMs
 
+// fast paths for power-of-two lengths (evx_fast.cu); return false if not applicable
+bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err);
+bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err);
+bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err);
+bool fast_paths_enabled();  // false when the environment sets EVX_GENERIC=1
+
 size_t spass_smem(int L);
 size_t xupdate_smem(int L);
 size_t zpass_smem(int M, int PZ, int rows);

@@ -13,6 +13,7 @@
 //   x pass + update    W, S -> S : F_x both, c_hat' = a c_hat + b g_hat, F_x^-1 / nx
 // with a = 1/(1 + dt M kappa |k|^4), b = -dt M |k|^2 a.
 #include <cstdint>
+#include <cstdlib>
 
 #include "evx_internal.h"
 
@@ -233,7 +234,12 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
         }
         __syncthreads();
         fft_tile<1, false>(Tile{tile, M, rows, 1, PZ}, a.plan, tws);
-        const float cb = a.cbar ? (float)(*a.cbar) : 0.f;
+        // mean split into FP32 hi + lo parts: c = (z s + lo) + hi rounds once at
+        // the scale of c without a common bias (adding (float)cbar alone would
+        // shift every voxel by the same rounding error of cbar)
+        const double cbd = a.cbar ? *a.cbar : 0.0;
+        const float cb = (float)cbd;
+        const float cbl = (float)(cbd - (double)cb);
         const float s = a.scale;
         double acc = 0.0;
         for (int e = threadIdx.x; e < nr * M; e += NT) {
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
                 const float d0 = fmaf(3.f * cn.x, cn.x, -1.f), d1 = fmaf(3.f * cn.y, cn.y, -1.f);
                 tile[r * PZ + n] = make_float2(z.x * s * d0, z.y * s * d1);
             } else {
-                const float c0 = fmaf(z.x, s, cb), c1 = fmaf(z.y, s, cb);
+                const float c0 = fmaf(z.x, s, cbl) + cb, c1 = fmaf(z.y, s, cbl) + cb;
                 if (MODE == Z_STEP) {
                     if (a.rout)
                         reinterpret_cast<float2*>(a.rout + (row0 + r) * a.rpitch)[n] = make_float2(c0, c1);
@@ -339,7 +345,18 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+bool fast_paths_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = getenv("EVX_GENERIC");
+        on = (e && e[0] == '1') ? 0 : 1;
+    }
+    return on == 1;
+}
+
 cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st) {
+    cudaError_t fe;
+    if (fast_paths_enabled() && fast_spass(a, dir, st, &fe)) return fe;
     const size_t sm = spass_smem(a.L);
     dim3 grid(a.nchunks, a.nouter);
     cudaError_t e;
@@ -354,6 +371,8 @@ cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st) {
 }
 
 cudaError_t launch_xupdate(const XUpdArgs& a, cudaStream_t st) {
+    cudaError_t fe;
+    if (fast_paths_enabled() && fast_xupdate(a, st, &fe)) return fe;
     const size_t sm = xupdate_smem(a.L);
     cudaError_t e;
     if ((e = set_smem(xupdate_kernel, sm)) != cudaSuccess) return e;
@@ -376,6 +395,8 @@ int zpass_grid(const ZPassArgs& a) {
 }
 
 cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st) {
+    cudaError_t fe;
+    if (mode == Z_STEP && fast_paths_enabled() && fast_zstep(a, st, &fe)) return fe;
     const size_t sm = zpass_smem(a.M, a.PZ, a.rows_per_cta);
     const int grid = zpass_grid(a);
     cudaError_t e = cudaSuccess;

@@ -45,7 +45,10 @@ def gpu_run(evx, c0, nsteps, **params):
 
 
 # sizes that span several tiles, ragged column chunks and radix 3 / 5 stages
+# (generic kernels), and power-of-two edges 64 .. 1024 (fast kernels, every
+# threads-per-pencil variant, x, y and z)
 SMALL = [(8, 8, 8), (16, 32, 64), (48, 40, 36), (24, 30, 50), (64, 64, 64)]
+POW2 = [(64, 128, 256), (256, 512, 128), (512, 64, 1024), (1024, 256, 64), (128, 1024, 512)]
 
 
 @pytest.mark.parametrize("shape", SMALL + [(400, 16, 20), (10, 1024, 12)])
@@ -61,7 +64,7 @@ def test_roundtrip(evx, shape):
     assert abs(mean - c.astype(np.float64).mean()) < 1e-15
 
 
-@pytest.mark.parametrize("shape", SMALL + [(128, 128, 128)])
+@pytest.mark.parametrize("shape", SMALL + POW2 + [(128, 128, 128)])
 def test_one_step_vs_oracle(evx, shape):
     c0 = inputs.uniform_field(shape, seed=0)
     ref = O.ch_step(c0, DT, M, KAPPA, H, 1)
@@ -69,7 +72,7 @@ def test_one_step_vs_oracle(evx, shape):
     assert rel_l2(got, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("shape", [(64, 64, 64), (48, 40, 36), (128, 128, 128)])
+@pytest.mark.parametrize("shape", [(64, 64, 64), (48, 40, 36), (128, 128, 128), (64, 128, 256)])
 def test_100_steps_vs_oracle(evx, shape):
     c0 = inputs.uniform_field(shape, seed=0)
     ref = O.ch_step(c0, DT, M, KAPPA, H, 100, check_imag=False)
@@ -148,6 +151,31 @@ def test_graph_and_profiled_paths_identical(evx):
             assert all(m > 0 for m in ms)
         g.close()
     assert torch.equal(outs[0], outs[1])
+
+
+def test_fast_and_generic_kernels_agree(evx, tmp_path):
+    """The power-of-two fast kernels and the generic mixed-radix kernels (forced
+    with EVX_GENERIC=1 in a child process) give the same field to FP32 rounding."""
+    import subprocess
+    import sys
+    import torch
+    shape = (128, 256, 512)
+    c0 = inputs.uniform_field(shape, seed=8, offset=0.2)
+    got = gpu_run(evx, c0, 10)
+    script = (
+        "import sys, numpy as np, torch\n"
+        "sys.path.insert(0, %r)\n"
+        "from paper_2507_21748_gb300 import evx, inputs\n"
+        "c0 = inputs.uniform_field(%r, seed=8, offset=0.2)\n"
+        "g = evx.Grid(%r, dt=0.1, M=1.0, kappa=1.0, h=1.0)\n"
+        "g.set_field(torch.from_numpy(c0).cuda()); g.step(10)\n"
+        "np.save(%r, g.get_field().cpu().numpy())\n"
+    ) % (str(__import__("os").path.dirname(__import__("os").path.dirname(__file__))), shape, shape,
+         str(tmp_path / "gen.npy"))
+    env = dict(__import__("os").environ, EVX_GENERIC="1")
+    subprocess.run([sys.executable, "-c", script], check=True, env=env)
+    gen = np.load(tmp_path / "gen.npy")
+    assert rel_l2(got, gen) <= 2e-6
 
 
 def test_host_io_matches_device_io(evx):

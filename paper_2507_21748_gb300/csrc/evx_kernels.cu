@@ -198,11 +198,21 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
     const int H = M / 2 + 1;  // pairs (k, M - k), k = 0 .. M/2
 
     if (MODE == Z_R2C) {
-        // real row of nz = 2M floats read as M complex z[n] = x[2n] + i x[2n+1]
+        // real row of nz = 2M floats read as M complex z[n] = x[2n] + i x[2n+1].
+        // With a.cbar set, the FP64 mean is subtracted first ((x - hi) - lo; x - hi
+        // is exact for x within a factor 2 of hi): the transforms then never carry
+        // the large k = 0 sums whose FP32 roundoff would spill into the other modes.
+        const double cbd = a.cbar ? *a.cbar : 0.0;
+        const float cb = (float)cbd;
+        const float cbl = (float)(cbd - (double)cb);
         for (int e = threadIdx.x; e < rows * M; e += NT) {
             const int r = e / M, n = e - r * M;
-            tile[r * PZ + n] = r < nr ? reinterpret_cast<const float2*>(a.rin + (row0 + r) * a.rpitch)[n]
-                                      : make_float2(0.f, 0.f);
+            float2 x = make_float2(0.f, 0.f);
+            if (r < nr) {
+                x = reinterpret_cast<const float2*>(a.rin + (row0 + r) * a.rpitch)[n];
+                x = make_float2((x.x - cb) - cbl, (x.y - cb) - cbl);
+            }
+            tile[r * PZ + n] = x;
         }
         __syncthreads();
     } else {
@@ -240,6 +250,8 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
         const double cbd = a.cbar ? *a.cbar : 0.0;
         const float cb = (float)cbd;
         const float cbl = (float)(cbd - (double)cb);
+        const float gp = (float)(3.0 * cbd * cbd - 1.0);  // g'(cbar)
+        const float c3 = (float)(3.0 * cbd);
         const float s = a.scale;
         double acc = 0.0;
         for (int e = threadIdx.x; e < nr * M; e += NT) {
@@ -254,7 +266,9 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
                 if (MODE == Z_STEP) {
                     if (a.rout)
                         reinterpret_cast<float2*>(a.rout + (row0 + r) * a.rpitch)[n] = make_float2(c0, c1);
-                    tile[r * PZ + n] = make_float2(c0 * fmaf(c0, c0, -1.f), c1 * fmaf(c1, c1, -1.f));
+                    // g(c) - g(cbar) from d = c - cbar (see the fast z pass)
+                    const float d0 = z.x * s, d1 = z.y * s;
+                    tile[r * PZ + n] = make_float2(d0 * fmaf(d0, c3 + d0, gp), d1 * fmaf(d1, c3 + d1, gp));
                 } else {  // Z_C2R
                     if (a.rout)
                         reinterpret_cast<float2*>(a.rout + (row0 + r) * a.rpitch)[n] = make_float2(c0, c1);

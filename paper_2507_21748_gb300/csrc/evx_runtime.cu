@@ -357,6 +357,7 @@ static evx_status load_real(evx_grid* g, const float* rows, long long pitch) {
     z.rin = rows;
     z.rpitch = pitch;
     z.out = g->W;
+    z.cbar = g->d_scal;  // transform c - cbar
     CK(launch_zpass(z, Z_R2C, g->st));
     CK(launch_spass(y_args(g, g->W, g->W), -1, g->st));
     // x pass with a = 1, b = 0: removes the k = 0 mode (carried in FP64)

@@ -55,9 +55,10 @@ def test_sampled_modes_one_step(evx, grid):
     # scale: typical amplitude of a noise mode, sqrt(V) * std(c0)
     scale = np.sqrt(float(N) ** 3) * 0.1 / np.sqrt(12.0)
     err = np.abs(got - expect)
-    # k = 0: sum of the FP32 field; the FP64 mean is carried exactly, so only the
-    # unbiased per-voxel FP32 rounding remains (std ~ sqrt(V) ulp(0.3) / sqrt(12) ~ 3e-4)
-    assert err[0] < 1e-2, err[0]
+    # k = 0: FP64 sum of the FP32 output field. The mass itself is carried in
+    # FP64 exactly (checked bitwise elsewhere); the FP32 field only adds its
+    # rounding and the FP32 transforms' roundoff that lands on the mean
+    assert err[0] / abs(expect[0]) < 1e-9, err[0]
     assert err[1:].max() / scale <= 1e-5, (err / scale)
 
 

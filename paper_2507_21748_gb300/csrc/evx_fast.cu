@@ -446,11 +446,11 @@ static int tp_of(int L) {
     }
 }
 
-// pencils per column tile: 4 (32-byte row pieces, 128-thread CTAs, two per SM
-// at L = 1024) for the long pencils, 8 below
+// pencils per column tile: 8, i.e. 64-byte row segments. (Four pencils, 32-byte
+// halves taken by different tiles, measured about 30% DRAM over-fetch.)
 template <int TP>
 struct Cols {
-    static constexpr int P = TP == 32 ? 4 : 8;
+    static constexpr int P = 8;
 };
 
 template <int TP, int DIR>

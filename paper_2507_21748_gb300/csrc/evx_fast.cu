@@ -396,14 +396,10 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
 
 // --------------------------------------------------------------- dispatch
 static int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
 }
 
 // set the kernel's shared-memory limit and return its resident CTAs per SM
@@ -411,6 +407,7 @@ static int num_sms() {
 // the cache is keyed by the function address)
 struct PrepEntry {
     const void* fn;
+    int dev;
     size_t smem;
     int nb;
 };
@@ -419,8 +416,10 @@ static cudaError_t prep(K kernel, size_t smem, int threads, int* grid_per_sm) {
     static PrepEntry cache[64];
     static int ncache = 0;
     const void* key = (const void*)kernel;
+    int dev = 0;
+    cudaGetDevice(&dev);
     for (int i = 0; i < ncache; ++i)
-        if (cache[i].fn == key && cache[i].smem == smem) {
+        if (cache[i].fn == key && cache[i].dev == dev && cache[i].smem == smem) {
             *grid_per_sm = cache[i].nb;
             return cudaSuccess;
         }
@@ -430,7 +429,7 @@ static cudaError_t prep(K kernel, size_t smem, int threads, int* grid_per_sm) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem);
     if (e != cudaSuccess) return e;
     nb = nb > 0 ? nb : 1;
-    if (ncache < 64) cache[ncache++] = PrepEntry{key, smem, nb};
+    if (ncache < 64) cache[ncache++] = PrepEntry{key, dev, smem, nb};
     *grid_per_sm = nb;
     return cudaSuccess;
 }

@@ -217,6 +217,7 @@ class CHSolve(torch.autograd.Function):
         ctx.ckpt_every = ckpt_every
         ctx.kappa = float(kappa)
         ctx.M = float(M)
+        ctx.param_like = (kappa, M)
         ctx.save_for_backward(c0c)
         return cN
 
@@ -226,9 +227,14 @@ class CHSolve(torch.autograd.Function):
         grid = ctx.grid
         grid.set_params(kappa=ctx.kappa, M=ctx.M)
         g0, gk, gm = grid.adjoint(c0, ctx.n_steps, ctx.ckpt_every, grad_out.contiguous().float())
-        dev = grad_out.device
-        return (g0, torch.tensor(gk, dtype=torch.float64, device=dev),
-                torch.tensor(gm, dtype=torch.float64, device=dev), None, None, None)
+
+        def like(v, ref):
+            if isinstance(ref, torch.Tensor):
+                return torch.tensor(v, dtype=ref.dtype, device=ref.device).reshape(ref.shape)
+            return None
+
+        kappa, M = ctx.param_like
+        return g0, like(gk, kappa), like(gm, M), None, None, None
 
 
 def ch_solve(c0, kappa, M, grid, n_steps, ckpt_every=20):

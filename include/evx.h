@@ -150,6 +150,27 @@ evx_status evx_pass_times(evx_grid *g, double *ms, long long *counts, int reset)
  * and output element once): pass index as in evx_pass_times. */
 evx_status evx_pass_bytes(const evx_grid *g, int pass, double *bytes);
 
+/* Allocation-free variant of evx_set_field + evx_ch_step + evx_get_field for
+ * callers that cannot allocate device memory (a process whose device memory
+ * is owned by another runtime, code that must not grow its footprint after
+ * start-up, callbacks that may not call cudaMalloc). The paper has no
+ * counterpart; it is a deployment convenience around the same kernels.
+ * Reads d_c_in (device, nx*ny*nz float32), advances n_steps steps with p and
+ * writes d_c_out (device, same layout; may equal d_c_in). All scratch - the
+ * two half-spectrum buffers, FP64 scalars, reduction partials, tables - lives
+ * in one static device array of 8 MiB that every GPU loading the library
+ * holds until the process exits; grids above 64^3 = 262144 voxels return
+ * EVX_ERR_SIZE (size rules otherwise as above). No cudaMalloc/cudaFree or
+ * allocating library call is made. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and should happen before any
+ * stream capture. Work is issued asynchronously on cuda_stream. Every call
+ * shares the array (its contents persist between calls; the call clears what
+ * must start at zero), so calls that overlap on the GPU - e.g. on two streams
+ * - race and must be serialised by the caller. Errors: EVX_ERR_ARG,
+ * EVX_ERR_SIZE, EVX_ERR_CUDA; message via evx_last_error(NULL). */
+evx_status evx_ch_step_static(const float *d_c_in, float *d_c_out, int nx, int ny, int nz,
+                              evx_params p, int n_steps, void *cuda_stream);
+
 /* Last error message of g (or of the calling thread when g is NULL). */
 const char *evx_last_error(const evx_grid *g);
 

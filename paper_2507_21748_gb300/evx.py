@@ -22,7 +22,7 @@ EXPORTS = [
     "evx_grid_create", "evx_grid_destroy", "evx_set_params", "evx_set_stream", "evx_set_field",
     "evx_set_field_host", "evx_get_field", "evx_get_field_host", "evx_ch_step", "evx_energy",
     "evx_mean", "evx_ch_adjoint", "evx_footprint", "evx_set_profiling", "evx_pass_times",
-    "evx_pass_bytes", "evx_last_error",
+    "evx_pass_bytes", "evx_ch_step_static", "evx_last_error",
 ]
 
 
@@ -61,6 +61,7 @@ def _load():
         "evx_set_profiling": ([vp, i], st),
         "evx_pass_times": ([vp, dp, ctypes.POINTER(ctypes.c_longlong), i], st),
         "evx_pass_bytes": ([vp, i, dp], st),
+        "evx_ch_step_static": ([fp, fp, i, i, i, Params, i, vp], st),
         "evx_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -197,6 +198,21 @@ class Grid:
                                     ctypes.c_void_p(dLdc0.data_ptr()), ctypes.byref(gk),
                                     ctypes.byref(gm)))
         return dLdc0, gk.value, gm.value
+
+
+def ch_step_static(c_in, c_out, n_steps, dt=0.1, M=1.0, kappa=1.0, h=1.0, stream=None):
+    """Allocation-free step (evx_ch_step_static): c_out <- n_steps steps from c_in.
+
+    Scratch lives in the library's static device array (grids up to 64^3);
+    calls share it, so they must not overlap on the GPU."""
+    shape = tuple(c_in.shape)
+    _check_field(c_in, shape)
+    _check_field(c_out, shape)
+    s = lib.evx_ch_step_static(ctypes.c_void_p(c_in.data_ptr()), ctypes.c_void_p(c_out.data_ptr()),
+                               *shape, Params(dt, M, kappa, h), int(n_steps), _stream_handle(stream))
+    if s != EVX_OK:
+        raise EvxError(s, lib.evx_last_error(None).decode())
+    return c_out
 
 
 class CHSolve(torch.autograd.Function):

@@ -12,6 +12,9 @@
 // both ownerships (each warp touches whole 64-byte row segments), the next
 // tile is prefetched into shared memory with cp.async while the current one
 // is computed, and the CTAs are persistent (one wave).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "evx_internal.h"
@@ -392,6 +395,240 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
     }
 }
 
+
+// ------------------------------------------------------------ TMA helpers
+// Tile loads and stores of the strided passes go through the tensor memory
+// accelerator: one thread issues cp.async.bulk.tensor boxes of up to 256 rows
+// of 8 complex values (64 bytes); loads complete on an mbarrier, stores are
+// bulk groups read out of a shared-memory staging tile. Every wait is bounded:
+// on timeout the kernel records it in g_timeout and leaves its tile loop.
+__device__ int g_timeout;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// wait for the phase of the given parity; false after about 2^32 cycles (~2 s)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1LL << 32)) return false;
+    }
+}
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store3(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// y pass with TMA: tensor dims {ncols, L, nouter}, boxes {8, BOX, 1}
+template <int TP, int DIR>
+__global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int ntiles,
+                                                            const __grid_constant__ CUtensorMap min,
+                                                            const __grid_constant__ CUtensorMap mout) {
+    constexpr int L = 32 * TP, NB = 32 / TP, XB = (L + TP) * 8, BOX = L < 256 ? L : 256, NBOX = L / BOX;
+    extern __shared__ __align__(1024) float4 smem4[];
+    float2* buf = reinterpret_cast<float2*>(smem4);  // [L][8] TMA destination
+    float2* xb = buf + L * 8;                         // transpose, then store staging
+    float2* tws = xb + XB;                            // [L] twiddles
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tws + L);
+    const int p = threadIdx.x & 7, n2 = threadIdx.x >> 3;
+    const int nchunks = a.nchunks;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    for (int i = threadIdx.x; i < L; i += 8 * TP) tws[i] = a.tw[i];
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    auto issue = [&](int tl) {
+        const int outer = tl / nchunks, chunk = tl - outer * nchunks;
+        fence_async_smem();
+        mbar_expect_tx(bar, L * 8 * sizeof(float2));
+#pragma unroll
+        for (int b = 0; b < NBOX; ++b) tma_load3(buf + b * BOX * 8, &min, chunk * 8, b * BOX, outer, bar);
+    };
+    if (threadIdx.x == 0) issue(tile);
+    uint32_t parity = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        const bool ok = mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
+            break;
+        }
+        parity ^= 1;
+        float2 v[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) v[n1] = buf[(n2 + TP * n1) * 8 + p];
+        if (threadIdx.x == 0) bulk_wait_read0();  // previous store has left the staging tile
+        __syncthreads();
+        const int next = tile + gridDim.x;
+        if (threadIdx.x == 0 && next < ntiles) issue(next);
+        Dft<32, DIR>::run(v);
+        twiddle_a<DIR>(v, n2, tws);
+        t1_s<TP, 8>(v, xb, n2, p);
+        pass_b<TP, DIR>(v);
+        __syncthreads();  // transpose reads done: xb becomes the store staging tile
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) xb[(n2 * NB + i + 32 * c) * 8 + p] = v[i * TP + c];
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int outer = tile / nchunks, chunk = tile - outer * nchunks;
+#pragma unroll
+            for (int b = 0; b < NBOX; ++b) tma_store3(&mout, chunk * 8, b * BOX, outer, xb + b * BOX * 8);
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) bulk_wait0();
+}
+
+// x pass + update with TMA: tensor dims {ncols, ny, nx}, boxes {8, 1, BOX}
+template <int TP>
+__global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int ntiles,
+                                                              const __grid_constant__ CUtensorMap mW,
+                                                              const __grid_constant__ CUtensorMap mS,
+                                                              const __grid_constant__ CUtensorMap mO) {
+    constexpr int L = 32 * TP, NB = 32 / TP, XB = (L + TP) * 8, BOX = L < 256 ? L : 256, NBOX = L / BOX;
+    extern __shared__ __align__(1024) float4 smem4[];
+    float2* bufW = reinterpret_cast<float2*>(smem4);
+    float2* bufS = bufW + L * 8;
+    float2* xb = bufS + L * 8;
+    float2* tws = xb + XB;
+    float* k2xs = reinterpret_cast<float*>(tws + L);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(k2xs + L);  // [0] W, [1] S
+    const int p = threadIdx.x & 7, n2 = threadIdx.x >> 3;
+    const int nchunks = a.nchunks;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    for (int i = threadIdx.x; i < L; i += 8 * TP) {
+        tws[i] = a.tw[i];
+        k2xs[i] = a.k2x[i];
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(bars + 0, 1);
+        mbar_init(bars + 1, 1);
+    }
+    __syncthreads();
+    auto issue = [&](const CUtensorMap* m, float2* buf, uint64_t* bar, int tl) {
+        const int ky = tl / nchunks, chunk = tl - ky * nchunks;
+        fence_async_smem();
+        mbar_expect_tx(bar, L * 8 * sizeof(float2));
+#pragma unroll
+        for (int b = 0; b < NBOX; ++b) tma_load3(buf + b * BOX * 8, m, chunk * 8, ky, b * BOX, bar);
+    };
+    if (threadIdx.x == 0) {
+        issue(&mW, bufW, bars + 0, tile);
+        issue(&mS, bufS, bars + 1, tile);
+    }
+    uint32_t parity = 0;
+    const float ndtM = -a.dtM;
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int ky = tile / nchunks, chunk = tile - ky * nchunks;
+        const int next = tile + gridDim.x;
+        // ---- g_hat = F_x W, kept as G = -dt M |k|^2 g_hat
+        bool ok = mbar_wait(bars + 0, parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
+            break;
+        }
+        float2 v[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufW[(n2 + TP * n1) * 8 + p];
+        if (threadIdx.x == 0) bulk_wait_read0();
+        __syncthreads();
+        if (threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
+        Dft<32, -1>::run(v);
+        twiddle_a<-1>(v, n2, tws);
+        t1_s<TP, 8>(v, xb, n2, p);
+        pass_b<TP, -1>(v);
+        const int kz = chunk * 8 + p;
+        const bool valid = kz < a.ncols;
+        const float k2yz = a.k2y[ky] + (valid ? a.k2z[kz] : 0.f);
+        float2 G[32];
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) {
+                const float f = ndtM * (k2xs[n2 * NB + i + 32 * c] + k2yz);
+                G[i * TP + c] = cscale(v[i * TP + c], f);
+            }
+        // ---- c_hat = F_x S
+        ok = mbar_wait(bars + 1, parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
+            break;
+        }
+        parity ^= 1;
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufS[(n2 + TP * n1) * 8 + p];
+        __syncthreads();
+        if (threadIdx.x == 0 && next < ntiles) issue(&mS, bufS, bars + 1, next);
+        Dft<32, -1>::run(v);
+        twiddle_a<-1>(v, n2, tws);
+        t1_s<TP, 8>(v, xb, n2, p);
+        pass_b<TP, -1>(v);
+        // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L; k = 0 stays out
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) {
+                const float k2 = k2xs[n2 * NB + i + 32 * c] + k2yz;
+                const float f = a.invL * rcp_approx(fmaf(a.dtMk, k2 * k2, 1.f));
+                v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), f);
+            }
+        if (ky == 0 && kz == 0 && n2 == 0) v[0] = make_float2(0.f, 0.f);
+        // ---- S' = F_x^-1 c_hat'
+        pass_b<TP, 1>(v);
+        twiddle_b<TP, 1>(v, n2, tws);
+        __syncthreads();
+        t2_s<TP, 8>(v, xb, n2, p);
+        Dft<32, 1>::run(v);
+        __syncthreads();  // transpose reads done: xb becomes the store staging tile
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) xb[(n2 + TP * n1) * 8 + p] = v[n1];
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int b = 0; b < NBOX; ++b) tma_store3(&mO, chunk * 8, ky, b * BOX, xb + b * BOX * 8);
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) bulk_wait0();
+}
+
 }  // namespace fast
 
 // --------------------------------------------------------------- dispatch
@@ -445,6 +682,96 @@ static int tp_of(int L) {
     }
 }
 
+
+// ------------------------------------------------------- tensor maps (host)
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3D map of a half-spectrum buffer: dims {ncols, d1, d2} with byte strides
+// s1, s2 (complex64 as 8-byte elements), box {8, b1, b2}
+static bool make_map(CUtensorMap* m, const void* base, int ncols, long long d1, long long s1, long long d2,
+                     long long s2, int b1, int b2) {
+    auto fn = encode_fn();
+    if (!fn || ((uintptr_t)base & 15) || (s1 & 15) || (s2 & 15)) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)ncols, (cuuint64_t)d1, (cuuint64_t)d2};
+    cuuint64_t strides[2] = {(cuuint64_t)s1, (cuuint64_t)s2};
+    cuuint32_t box[3] = {8, (cuuint32_t)b1, (cuuint32_t)b2};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool fast_timeout_flag(int* flag, bool clear) {
+    int h = 0;
+    if (cudaMemcpyFromSymbol(&h, fast::g_timeout, sizeof(int)) != cudaSuccess) return false;
+    if (clear && h) {
+        int z = 0;
+        cudaMemcpyToSymbol(fast::g_timeout, &z, sizeof(int));
+    }
+    *flag = h;
+    return true;
+}
+
+template <int TP, int DIR>
+static bool run_fspass_tma(const SPassArgs& a, cudaStream_t st, cudaError_t* err) {
+    constexpr int L = 32 * TP, BOX = L < 256 ? L : 256;
+    CUtensorMap mi, mo;
+    const long long s1 = a.rs * 8, s2 = a.os * 8;
+    if (!make_map(&mi, a.in, a.ncols, a.L, s1, a.nouter, s2, BOX, 1) ||
+        !make_map(&mo, a.out, a.ncols, a.L, s1, a.nouter, s2, BOX, 1))
+        return false;
+    const size_t smem = sizeof(float2) * (L * 8 + (L + TP) * 8 + L) + 16;
+    int per = 0;
+    cudaError_t e = prep(fast::fspass_tma_kernel<TP, DIR>, smem, 8 * TP, &per);
+    if (e != cudaSuccess) {
+        *err = e;
+        return true;
+    }
+    const int ntiles = a.nchunks * a.nouter;
+    const int grid = std::min(ntiles, per * num_sms());
+    fast::fspass_tma_kernel<TP, DIR><<<grid, 8 * TP, smem, st>>>(a, ntiles, mi, mo);
+    *err = cudaGetLastError();
+    return true;
+}
+
+template <int TP>
+static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
+    constexpr int L = 32 * TP, BOX = L < 256 ? L : 256;
+    CUtensorMap mw, ms, mo;
+    const long long s1 = a.os * 8, s2 = a.rs * 8;  // dims {ncols, ny, nx}
+    if (!make_map(&mw, a.W, a.ncols, a.ny, s1, a.L, s2, 1, BOX) ||
+        !make_map(&ms, a.S, a.ncols, a.ny, s1, a.L, s2, 1, BOX) ||
+        !make_map(&mo, a.S_out, a.ncols, a.ny, s1, a.L, s2, 1, BOX))
+        return false;
+    const size_t smem = sizeof(float2) * (2 * L * 8 + (L + TP) * 8 + L) + sizeof(float) * L + 16;
+    int per = 0;
+    cudaError_t e = prep(fast::fxupd_tma_kernel<TP>, smem, 8 * TP, &per);
+    if (e != cudaSuccess) {
+        *err = e;
+        return true;
+    }
+    const int ntiles = a.nchunks * a.ny;
+    const int grid = std::min(ntiles, per * num_sms());
+    fast::fxupd_tma_kernel<TP><<<grid, 8 * TP, smem, st>>>(a, ntiles, mw, ms, mo);
+    *err = cudaGetLastError();
+    return true;
+}
+
 // pencils per column tile: 8, i.e. 64-byte row segments. (Four pencils, 32-byte
 // halves taken by different tiles, measured about 30% DRAM over-fetch.)
 template <int TP>
@@ -472,6 +799,8 @@ bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err) 
     if (!TP) return false;
 #define CASE(T)                                                                       \
     case T:                                                                           \
+        if (dir < 0 ? run_fspass_tma<T, -1>(a, st, err) : run_fspass_tma<T, 1>(a, st, err)) \
+            return true;                                                              \
         *err = dir < 0 ? run_fspass<T, -1>(a, st) : run_fspass<T, 1>(a, st);          \
         return true;
     switch (TP) {
@@ -500,11 +829,11 @@ bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
     const int TP = tp_of(a.L);
     if (!TP || a.W == nullptr) return false;
     switch (TP) {
-        case 2: *err = run_fxupd<2>(a, st); return true;
-        case 4: *err = run_fxupd<4>(a, st); return true;
-        case 8: *err = run_fxupd<8>(a, st); return true;
-        case 16: *err = run_fxupd<16>(a, st); return true;
-        case 32: *err = run_fxupd<32>(a, st); return true;
+        case 2: if (!run_fxupd_tma<2>(a, st, err)) *err = run_fxupd<2>(a, st); return true;
+        case 4: if (!run_fxupd_tma<4>(a, st, err)) *err = run_fxupd<4>(a, st); return true;
+        case 8: if (!run_fxupd_tma<8>(a, st, err)) *err = run_fxupd<8>(a, st); return true;
+        case 16: if (!run_fxupd_tma<16>(a, st, err)) *err = run_fxupd<16>(a, st); return true;
+        case 32: if (!run_fxupd_tma<32>(a, st, err)) *err = run_fxupd<32>(a, st); return true;
     }
     return false;
 }

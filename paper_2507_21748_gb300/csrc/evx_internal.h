@@ -97,6 +97,8 @@ bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err);
 bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err);
 bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err);
 bool fast_paths_enabled();  // false when the environment sets EVX_GENERIC=1
+// reads (and optionally clears) the flag a bounded TMA wait sets when it gives up
+bool fast_timeout_flag(int* flag, bool clear);
 
 size_t spass_smem(int L);
 size_t xupdate_smem(int L);

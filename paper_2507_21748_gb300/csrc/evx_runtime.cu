@@ -212,6 +212,14 @@ static evx_status drain_events(evx_grid* g) {
     return EVX_OK;
 }
 
+// after a synchronisation: report a bounded wait that gave up in a fast kernel
+static evx_status check_timeouts(evx_grid* g) {
+    int f = 0;
+    if (fast_timeout_flag(&f, true) && f)
+        return fail(g, EVX_ERR_CUDA, "a bounded TMA wait timed out in a fast kernel; results are invalid");
+    return EVX_OK;
+}
+
 static evx_status build_graph(evx_grid* g, int nsteps, cudaGraphExec_t* out) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
@@ -413,7 +421,7 @@ evx_status evx_get_field_host(evx_grid* g, float* h_out) {
     CK(cudaMemcpy2DAsync(h_out, sizeof(float) * g->nz, g->W, sizeof(float) * 2 * g->Zp,
                          sizeof(float) * g->nz, nrows, cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
-    return EVX_OK;
+    return check_timeouts(g);
 }
 
 evx_status evx_ch_step(evx_grid* g, int n_steps) {
@@ -489,6 +497,8 @@ evx_status evx_energy(evx_grid* g, double* E, double* mass) {
     double host[3];
     CK(cudaMemcpyAsync(host, g->d_scal, sizeof host, cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
+    s = check_timeouts(g);
+    if (s != EVX_OK) return s;
     const double e = host[1] + host[2];
     if (!std::isfinite(e) || !std::isfinite(host[0]))
         return fail(g, EVX_ERR_NONFINITE, "field holds NaN or Inf (energy %g, mean %g)", e, host[0]);
@@ -502,7 +512,7 @@ evx_status evx_mean(evx_grid* g, double* cbar) {
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     CK(cudaMemcpyAsync(cbar, g->d_scal, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
-    return EVX_OK;
+    return check_timeouts(g);
 }
 
 evx_status evx_footprint(const evx_grid* g, size_t* bytes) {
@@ -525,6 +535,8 @@ evx_status evx_pass_times(evx_grid* g, double* ms, long long* counts, int reset)
     if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
     CK(cudaStreamSynchronize(g->st));
     evx_status s = drain_events(g);
+    if (s != EVX_OK) return s;
+    s = check_timeouts(g);
     if (s != EVX_OK) return s;
     for (int k = 0; k < 4; ++k) {
         if (ms) ms[k] = g->pass_ms[k];

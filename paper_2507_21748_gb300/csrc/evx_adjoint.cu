@@ -42,6 +42,8 @@ struct XAdjArgs {
     float2* T;
     int L;
     long long rs, os;
+    int YB;
+    long long os2;
     int ny, ncols, nchunks, M;
     Plan plan;
     const float2* tw;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(NT, 1) xadj_kernel(XAdjArgs a) {
     for (int i = threadIdx.x; i < L; i += NT) tws[i] = a.tw[i];
     const int chunk = blockIdx.x, ky = blockIdx.y;
     const int col0 = chunk * SP;
-    const long long base = (long long)ky * a.os + col0;
+    const long long base = split_off(ky, a.YB, a.os, a.os2) + col0;
     load_cols(tile, 0, a.Lam, base, a.rs, L, col0, a.ncols);
     load_cols(tile, SP, a.Sn1, base, a.rs, L, col0, a.ncols);
     __syncthreads();
@@ -302,6 +304,7 @@ extern "C" evx_status evx_ch_adjoint(evx_grid* g, const float* d_c0, int n_steps
         ZPassArgs z = z_args(g);
         z.rin = d_dLdcN;
         z.rpitch = g->nz;
+        z.map_rows = 1;
         z.out = g->W;
         CKA(launch_zpass(z, Z_R2C, st));
         CKA(launch_spass(y_args(g, g->W, A->Lam), -1, st));
@@ -310,8 +313,10 @@ extern "C" evx_status evx_ch_adjoint(evx_grid* g, const float* d_c0, int n_steps
     const double V = (double)g->nx * g->ny * g->nz;
     XAdjArgs xa{};
     xa.L = g->nx;
-    xa.rs = (long long)g->ny * g->Zp;
+    xa.rs = (long long)g->YB * g->Zp;
     xa.os = g->Zp;
+    xa.YB = g->YB;
+    xa.os2 = (long long)g->nx * g->YB * g->Zp;
     xa.ny = g->ny;
     xa.ncols = g->M + 1;
     xa.nchunks = g->Zp / SP;
@@ -371,6 +376,7 @@ extern "C" evx_status evx_ch_adjoint(evx_grid* g, const float* d_c0, int n_steps
         z.in = g->W;
         z.rout = d_dLdc0;
         z.rpitch = g->nz;
+        z.map_rows = 1;
         z.cbar = nullptr;
         CKA(launch_zpass(z, Z_C2R, st));
     }

@@ -9,9 +9,9 @@
 // the one shared-memory transpose thread j owns X[k1 + 32 k2] for
 // k1 in [j 32/TP, (j+1) 32/TP), all k2 ("block ownership"). The inverse walks the
 // same way back. Global loads and stores go straight from/to registers in
-// both ownerships (each warp touches whole 64-byte row segments), the next
-// tile is prefetched into shared memory with cp.async while the current one
-// is computed, and the CTAs are persistent (one wave).
+// both ownerships (each warp touches whole 64-byte row segments) for the z
+// pass, whose next tile is prefetched with cp.async; the x and y passes move
+// whole tiles with TMA (below). CTAs are persistent (one wave).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -130,166 +130,10 @@ __device__ __forceinline__ void t2_z(float2 (&v)[32], float2* xb, int n2, int r)
     for (int a = 0; a < 32; ++a) v[a] = xb[slot_z<TP>(r, n2, a)];
 }
 
-// prefetch one [L][P] column tile (rows rs apart) into buf as 16-byte
-// pieces; invalid columns are zero-filled
-template <int TP, int P>
-__device__ __forceinline__ void issue_tile(float2* buf, const float2* g, long long base, long long rs,
-                                           int col0, int ncols) {
-    constexpr int NT_ = P * TP, PR = P / 2;  // threads, pieces per row
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int e = threadIdx.x + k * NT_;
-        const int row = e / PR, q = e % PR;
-        const int nv = min(max(ncols - (col0 + 2 * q), 0), 2);
-        const float2* src = g + base + (long long)row * rs + 2 * q;
-        cp_async16(buf + row * P + 2 * q, nv ? src : g, nv * 8);
-    }
-    cp_commit();
-}
-
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
-}
-
-// ---------------------------------------------------------- y pass (strided)
-template <int TP, int P, int DIR>
-__global__ void __launch_bounds__(P * TP) fspass_kernel(SPassArgs a, int ntiles) {
-    constexpr int L = 32 * TP, NB = 32 / TP, XB = (L + TP) * P;
-    extern __shared__ float4 smem4[];
-    float2* buf = reinterpret_cast<float2*>(smem4);  // [L][P]
-    float2* xb = buf + L * P;                         // transpose
-    float2* tws = xb + XB;                            // [L] twiddles
-    const int p = threadIdx.x % P, n2 = threadIdx.x / P;
-    const int nchunks = a.nchunks;
-    int tile = blockIdx.x;
-    if (tile >= ntiles) return;
-    for (int i = threadIdx.x; i < L; i += P * TP) tws[i] = a.tw[i];
-    {
-        const int outer = tile / nchunks, chunk = tile - outer * nchunks;
-        issue_tile<TP, P>(buf, a.in, (long long)outer * a.os + chunk * P, a.rs, chunk * P, a.ncols);
-    }
-    for (; tile < ntiles; tile += gridDim.x) {
-        cp_wait<0>();
-        __syncthreads();
-        float2 v[32];
-#pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) v[n1] = buf[(n2 + TP * n1) * P + p];
-        __syncthreads();
-        const int next = tile + gridDim.x;
-        if (next < ntiles) {
-            const int outer = next / nchunks, chunk = next - outer * nchunks;
-            issue_tile<TP, P>(buf, a.in, (long long)outer * a.os + chunk * P, a.rs, chunk * P, a.ncols);
-        }
-        Dft<32, DIR>::run(v);
-        twiddle_a<DIR>(v, n2, tws);
-        t1_s<TP, P>(v, xb, n2, p);
-        pass_b<TP, DIR>(v);
-        const int outer = tile / nchunks, chunk = tile - outer * nchunks;
-        if (chunk * P + p < a.ncols) {
-            float2* out = a.out + (long long)outer * a.os + chunk * P + p;
-#pragma unroll
-            for (int i = 0; i < NB; ++i)
-#pragma unroll
-                for (int c = 0; c < TP; ++c) out[(long long)(n2 * NB + i + 32 * c) * a.rs] = v[i * TP + c];
-        }
-    }
-}
-
-// ------------------------------------------------- x pass + k-space update
-template <int TP, int P>
-__global__ void __launch_bounds__(P * TP, 8 / P) fxupd_kernel(XUpdArgs a, int ntiles) {
-    constexpr int L = 32 * TP, NB = 32 / TP, XB = (L + TP) * P;
-    extern __shared__ float4 smem4[];
-    float2* bufW = reinterpret_cast<float2*>(smem4);
-    float2* bufS = bufW + L * P;
-    float2* xb = bufS + L * P;
-    float2* tws = xb + XB;                               // [L] twiddles
-    float* k2xs = reinterpret_cast<float*>(tws + L);     // [L] |k_x|^2
-    const int p = threadIdx.x % P, n2 = threadIdx.x / P;
-    const int nchunks = a.nchunks;
-    int tile = blockIdx.x;
-    if (tile >= ntiles) return;
-    for (int i = threadIdx.x; i < L; i += P * TP) {
-        tws[i] = a.tw[i];
-        k2xs[i] = a.k2x[i];
-    }
-    {
-        const int ky = tile / nchunks, chunk = tile - ky * nchunks;
-        const long long base = (long long)ky * a.os + chunk * P;
-        issue_tile<TP, P>(bufW, a.W, base, a.rs, chunk * P, a.ncols);
-        issue_tile<TP, P>(bufS, a.S, base, a.rs, chunk * P, a.ncols);
-    }
-    const float ndtM = -a.dtM;
-    for (; tile < ntiles; tile += gridDim.x) {
-        const int ky = tile / nchunks, chunk = tile - ky * nchunks;
-        const int next = tile + gridDim.x;
-        long long nbase = 0;
-        int nchunk = 0;
-        if (next < ntiles) {
-            const int nky = next / nchunks;
-            nchunk = next - nky * nchunks;
-            nbase = (long long)nky * a.os + nchunk * P;
-        }
-        // ---- g_hat = F_x W, kept as G = -dt M |k|^2 g_hat
-        cp_wait<1>();
-        __syncthreads();
-        float2 v[32];
-#pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufW[(n2 + TP * n1) * P + p];
-        __syncthreads();
-        if (next < ntiles) issue_tile<TP, P>(bufW, a.W, nbase, a.rs, nchunk * P, a.ncols);
-        Dft<32, -1>::run(v);
-        twiddle_a<-1>(v, n2, tws);
-        t1_s<TP, P>(v, xb, n2, p);
-        pass_b<TP, -1>(v);
-        const int kz = chunk * P + p;
-        const bool valid = kz < a.ncols;
-        const float k2yz = a.k2y[ky] + (valid ? a.k2z[kz] : 0.f);
-        float2 G[32];
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-#pragma unroll
-            for (int c = 0; c < TP; ++c) {
-                const float f = ndtM * (k2xs[n2 * NB + i + 32 * c] + k2yz);
-                G[i * TP + c] = cscale(v[i * TP + c], f);
-            }
-        // ---- c_hat = F_x S
-        if (next < ntiles) cp_wait<1>(); else cp_wait<0>();
-        __syncthreads();
-#pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufS[(n2 + TP * n1) * P + p];
-        __syncthreads();
-        if (next < ntiles) issue_tile<TP, P>(bufS, a.S, nbase, a.rs, nchunk * P, a.ncols);
-        Dft<32, -1>::run(v);
-        twiddle_a<-1>(v, n2, tws);
-        t1_s<TP, P>(v, xb, n2, p);
-        pass_b<TP, -1>(v);
-        // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L;
-        //      the k = 0 mode stays out (the mean is carried in FP64)
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-#pragma unroll
-            for (int c = 0; c < TP; ++c) {
-                const float k2 = k2xs[n2 * NB + i + 32 * c] + k2yz;
-                const float f = a.invL * rcp_approx(fmaf(a.dtMk, k2 * k2, 1.f));
-                const float2 r = cadd(v[i * TP + c], G[i * TP + c]);
-                v[i * TP + c] = cscale(r, f);
-            }
-        if (ky == 0 && kz == 0 && n2 == 0) v[0] = make_float2(0.f, 0.f);
-        // ---- S' = F_x^-1 c_hat'
-        pass_b<TP, 1>(v);
-        twiddle_b<TP, 1>(v, n2, tws);
-        __syncthreads();  // transpose buffer reads of the forward done
-        t2_s<TP, P>(v, xb, n2, p);
-        Dft<32, 1>::run(v);
-        if (valid) {
-            float2* out = a.S_out + (long long)ky * a.os + chunk * P + p;
-#pragma unroll
-            for (int n1 = 0; n1 < 32; ++n1) out[(long long)(n2 + TP * n1) * a.rs] = v[n1];
-        }
-    }
 }
 
 // ------------------------------------------------ z pass: C2R, c^3 - c, R2C
@@ -431,16 +275,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         if (clock64() - t0 > (1LL << 32)) return false;
     }
 }
-__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+// 4D tensor {kz, y within block, x, y block} of a y-blocked half spectrum
+__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                           uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tma_store3(const CUtensorMap* map, int c0, int c1, int c2, const void* src) {
-    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+__device__ __forceinline__ void tma_store4(const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                           const void* src) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -452,7 +298,8 @@ __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// y pass with TMA: tensor dims {ncols, L, nouter}, boxes {8, BOX, 1}
+// y pass with TMA: boxes {8, 32 (y in block), 1 (x), BOX/32 (y blocks)} cover
+// BOX consecutive y rows of one x line (y blocks of 32 rows)
 template <int TP, int DIR>
 __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int ntiles,
                                                             const __grid_constant__ CUtensorMap min,
@@ -475,7 +322,7 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
         fence_async_smem();
         mbar_expect_tx(bar, L * 8 * sizeof(float2));
 #pragma unroll
-        for (int b = 0; b < NBOX; ++b) tma_load3(buf + b * BOX * 8, &min, chunk * 8, b * BOX, outer, bar);
+        for (int b = 0; b < NBOX; ++b) tma_load4(buf + b * BOX * 8, &min, chunk * 8, 0, outer, b * BOX / 32, bar);
     };
     if (threadIdx.x == 0) issue(tile);
     uint32_t parity = 0;
@@ -507,14 +354,15 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
         if (threadIdx.x == 0) {
             const int outer = tile / nchunks, chunk = tile - outer * nchunks;
 #pragma unroll
-            for (int b = 0; b < NBOX; ++b) tma_store3(&mout, chunk * 8, b * BOX, outer, xb + b * BOX * 8);
+            for (int b = 0; b < NBOX; ++b)
+                tma_store4(&mout, chunk * 8, 0, outer, b * BOX / 32, xb + b * BOX * 8);
             bulk_commit();
         }
     }
     if (threadIdx.x == 0) bulk_wait0();
 }
 
-// x pass + update with TMA: tensor dims {ncols, ny, nx}, boxes {8, 1, BOX}
+// x pass + update with TMA: boxes {8, 1, BOX (x), 1}
 template <int TP>
 __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int ntiles,
                                                               const __grid_constant__ CUtensorMap mW,
@@ -541,12 +389,14 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         mbar_init(bars + 1, 1);
     }
     __syncthreads();
+    const int YB = a.YB;
     auto issue = [&](const CUtensorMap* m, float2* buf, uint64_t* bar, int tl) {
         const int ky = tl / nchunks, chunk = tl - ky * nchunks;
         fence_async_smem();
         mbar_expect_tx(bar, L * 8 * sizeof(float2));
 #pragma unroll
-        for (int b = 0; b < NBOX; ++b) tma_load3(buf + b * BOX * 8, m, chunk * 8, ky, b * BOX, bar);
+        for (int b = 0; b < NBOX; ++b)
+            tma_load4(buf + b * BOX * 8, m, chunk * 8, ky % YB, b * BOX, ky / YB, bar);
     };
     if (threadIdx.x == 0) {
         issue(&mW, bufW, bars + 0, tile);
@@ -622,7 +472,8 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         __syncthreads();
         if (threadIdx.x == 0) {
 #pragma unroll
-            for (int b = 0; b < NBOX; ++b) tma_store3(&mO, chunk * 8, ky, b * BOX, xb + b * BOX * 8);
+            for (int b = 0; b < NBOX; ++b)
+                tma_store4(&mO, chunk * 8, ky % YB, b * BOX, ky / YB, xb + b * BOX * 8);
             bulk_commit();
         }
     }
@@ -701,17 +552,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3D map of a half-spectrum buffer: dims {ncols, d1, d2} with byte strides
-// s1, s2 (complex64 as 8-byte elements), box {8, b1, b2}
-static bool make_map(CUtensorMap* m, const void* base, int ncols, long long d1, long long s1, long long d2,
-                     long long s2, int b1, int b2) {
+// 4D map of a y-blocked half-spectrum buffer: dims {ncols, YB, nx, ny / YB}
+// (complex64 as 8-byte elements), box {8, b1, b2, b3}
+static bool make_map(CUtensorMap* m, const void* base, int ncols, int YB, int nx, int ny, long long Zp, int b1,
+                     int b2, int b3) {
     auto fn = encode_fn();
-    if (!fn || ((uintptr_t)base & 15) || (s1 & 15) || (s2 & 15)) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)ncols, (cuuint64_t)d1, (cuuint64_t)d2};
-    cuuint64_t strides[2] = {(cuuint64_t)s1, (cuuint64_t)s2};
-    cuuint32_t box[3] = {8, (cuuint32_t)b1, (cuuint32_t)b2};
-    cuuint32_t es[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, strides, box, es,
+    if (!fn || ((uintptr_t)base & 15) || (ny % YB)) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)ncols, (cuuint64_t)YB, (cuuint64_t)nx, (cuuint64_t)(ny / YB)};
+    cuuint64_t strides[3] = {(cuuint64_t)(Zp * 8), (cuuint64_t)(YB * Zp * 8), (cuuint64_t)((long long)nx * YB * Zp * 8)};
+    cuuint32_t box[4] = {8, (cuuint32_t)b1, (cuuint32_t)b2, (cuuint32_t)b3};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, const_cast<void*>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -730,10 +581,12 @@ bool fast_timeout_flag(int* flag, bool clear) {
 template <int TP, int DIR>
 static bool run_fspass_tma(const SPassArgs& a, cudaStream_t st, cudaError_t* err) {
     constexpr int L = 32 * TP, BOX = L < 256 ? L : 256;
+    // y pass geometry: rows y split in blocks of 32 (rs = Zp), lines x (os = 32 Zp)
+    if (a.YB != 32 || a.rs * 32 != a.os) return false;
+    const long long Zp = a.rs;
     CUtensorMap mi, mo;
-    const long long s1 = a.rs * 8, s2 = a.os * 8;
-    if (!make_map(&mi, a.in, a.ncols, a.L, s1, a.nouter, s2, BOX, 1) ||
-        !make_map(&mo, a.out, a.ncols, a.L, s1, a.nouter, s2, BOX, 1))
+    if (!make_map(&mi, a.in, a.ncols, 32, a.nouter, a.L, Zp, 32, 1, BOX / 32) ||
+        !make_map(&mo, a.out, a.ncols, 32, a.nouter, a.L, Zp, 32, 1, BOX / 32))
         return false;
     const size_t smem = sizeof(float2) * (L * 8 + (L + TP) * 8 + L) + 16;
     int per = 0;
@@ -752,11 +605,13 @@ static bool run_fspass_tma(const SPassArgs& a, cudaStream_t st, cudaError_t* err
 template <int TP>
 static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
     constexpr int L = 32 * TP, BOX = L < 256 ? L : 256;
+    // x pass geometry: rows x (rs = YB Zp), lines y split in blocks of YB (os = Zp)
+    if (a.os * a.YB != a.rs) return false;
+    const long long Zp = a.os;
     CUtensorMap mw, ms, mo;
-    const long long s1 = a.os * 8, s2 = a.rs * 8;  // dims {ncols, ny, nx}
-    if (!make_map(&mw, a.W, a.ncols, a.ny, s1, a.L, s2, 1, BOX) ||
-        !make_map(&ms, a.S, a.ncols, a.ny, s1, a.L, s2, 1, BOX) ||
-        !make_map(&mo, a.S_out, a.ncols, a.ny, s1, a.L, s2, 1, BOX))
+    if (!make_map(&mw, a.W, a.ncols, a.YB, a.L, a.ny, Zp, 1, BOX, 1) ||
+        !make_map(&ms, a.S, a.ncols, a.YB, a.L, a.ny, Zp, 1, BOX, 1) ||
+        !make_map(&mo, a.S_out, a.ncols, a.YB, a.L, a.ny, Zp, 1, BOX, 1))
         return false;
     const size_t smem = sizeof(float2) * (2 * L * 8 + (L + TP) * 8 + L) + sizeof(float) * L + 16;
     int per = 0;
@@ -772,37 +627,12 @@ static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) 
     return true;
 }
 
-// pencils per column tile: 8, i.e. 64-byte row segments. (Four pencils, 32-byte
-// halves taken by different tiles, measured about 30% DRAM over-fetch.)
-template <int TP>
-struct Cols {
-    static constexpr int P = 8;
-};
-
-template <int TP, int DIR>
-static cudaError_t run_fspass(const SPassArgs& a0, cudaStream_t st) {
-    constexpr int P = Cols<TP>::P, L = 32 * TP;
-    SPassArgs a = a0;
-    a.nchunks = a0.nchunks * 8 / P;  // chunks of P columns
-    const size_t smem = sizeof(float2) * (L * P + (L + TP) * P + L);
-    int per = 0;
-    cudaError_t e = prep(fast::fspass_kernel<TP, P, DIR>, smem, P * TP, &per);
-    if (e != cudaSuccess) return e;
-    const int ntiles = a.nchunks * a.nouter;
-    const int grid = std::min(ntiles, per * num_sms());
-    fast::fspass_kernel<TP, P, DIR><<<grid, P * TP, smem, st>>>(a, ntiles);
-    return cudaGetLastError();
-}
-
 bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err) {
     const int TP = tp_of(a.L);
     if (!TP) return false;
 #define CASE(T)                                                                       \
     case T:                                                                           \
-        if (dir < 0 ? run_fspass_tma<T, -1>(a, st, err) : run_fspass_tma<T, 1>(a, st, err)) \
-            return true;                                                              \
-        *err = dir < 0 ? run_fspass<T, -1>(a, st) : run_fspass<T, 1>(a, st);          \
-        return true;
+        return dir < 0 ? run_fspass_tma<T, -1>(a, st, err) : run_fspass_tma<T, 1>(a, st, err);
     switch (TP) {
         CASE(2) CASE(4) CASE(8) CASE(16) CASE(32)
     }
@@ -810,30 +640,15 @@ bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err) 
     return false;
 }
 
-template <int TP>
-static cudaError_t run_fxupd(const XUpdArgs& a0, cudaStream_t st) {
-    constexpr int P = Cols<TP>::P, L = 32 * TP;
-    XUpdArgs a = a0;
-    a.nchunks = a0.nchunks * 8 / P;
-    const size_t smem = sizeof(float2) * (2 * L * P + (L + TP) * P + L) + sizeof(float) * L;
-    int per = 0;
-    cudaError_t e = prep(fast::fxupd_kernel<TP, P>, smem, P * TP, &per);
-    if (e != cudaSuccess) return e;
-    const int ntiles = a.nchunks * a.ny;
-    const int grid = std::min(ntiles, per * num_sms());
-    fast::fxupd_kernel<TP, P><<<grid, P * TP, smem, st>>>(a, ntiles);
-    return cudaGetLastError();
-}
-
 bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
     const int TP = tp_of(a.L);
     if (!TP || a.W == nullptr) return false;
     switch (TP) {
-        case 2: if (!run_fxupd_tma<2>(a, st, err)) *err = run_fxupd<2>(a, st); return true;
-        case 4: if (!run_fxupd_tma<4>(a, st, err)) *err = run_fxupd<4>(a, st); return true;
-        case 8: if (!run_fxupd_tma<8>(a, st, err)) *err = run_fxupd<8>(a, st); return true;
-        case 16: if (!run_fxupd_tma<16>(a, st, err)) *err = run_fxupd<16>(a, st); return true;
-        case 32: if (!run_fxupd_tma<32>(a, st, err)) *err = run_fxupd<32>(a, st); return true;
+        case 2: return run_fxupd_tma<2>(a, st, err);
+        case 4: return run_fxupd_tma<4>(a, st, err);
+        case 8: return run_fxupd_tma<8>(a, st, err);
+        case 16: return run_fxupd_tma<16>(a, st, err);
+        case 32: return run_fxupd_tma<32>(a, st, err);
     }
     return false;
 }

@@ -12,6 +12,7 @@ struct AdjStore;  // adjoint segment store (evx_adjoint.cu)
 
 struct evx_grid {
     int nx = 0, ny = 0, nz = 0, M = 0, Zp = 0, PZ = 0, zrows = 0;
+    int YB = 0;                  // y block of the spectral layout (choose_yblock)
     evx_params p{};
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture

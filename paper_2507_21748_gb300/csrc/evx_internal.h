@@ -6,14 +6,30 @@
 
 namespace evx {
 
-// Strided pass: 1D transforms along an axis whose elements are rs complex
-// apart; a tile covers P adjacent columns (kz) of one "outer" line.
+// Spectral buffers are y-blocked: element (x, y, kz) of a half spectrum sits at
+//   ((y / YB * nx + x) * YB + y % YB) * Zp + kz      (complex64 units)
+// with YB = 32 when the y pass has a fast path (ny a power of two >= 64) and
+// YB = ny otherwise (plain [x][y][kz]). The x stride is then YB * Zp (at most
+// 133 KB at nz = 1024), so the 1024 rows of an x tile share a few 2 MB pages.
+inline int choose_yblock(int ny, bool fast) {
+    return (fast && ny >= 64 && ny <= 1024 && (ny & (ny - 1)) == 0) ? 32 : ny;
+}
+// offset of index i along an axis split into blocks of YB: i % YB steps of
+// s_in, i / YB steps of s_out
+__host__ __device__ inline long long split_off(long long i, int YB, long long s_in, long long s_out) {
+    return (i / YB) * s_out + (i % YB) * s_in;
+}
+
+// Strided pass: 1D transforms along y; a tile covers P adjacent columns (kz)
+// of one x line.
 struct SPassArgs {
     const float2* in;
     float2* out;        // may equal in
     int L;              // transform length
-    long long rs;       // stride between consecutive elements (complex)
+    long long rs;       // stride between consecutive elements within a block (complex)
     long long os;       // stride between consecutive outer lines (complex)
+    int YB;             // element i at split_off(i, YB, rs, os2)
+    long long os2;      // stride between element blocks
     int nouter;         // number of outer lines
     int ncols;          // valid columns (kz = 0 .. M)
     int nchunks;        // column chunks of P
@@ -27,8 +43,10 @@ struct XUpdArgs {
     float2* S;          // state: F_y F_z c (without the k = 0 mode), updated in place
     float2* S_out;      // where the new state goes (== S for a plain step)
     int L;              // nx
-    long long rs;       // ny * Zp (stride between consecutive x)
-    long long os;       // Zp (stride between consecutive y)
+    long long rs;       // stride between consecutive x (YB * Zp)
+    long long os;       // stride between consecutive y within a block (Zp)
+    int YB;             // line ky starts at split_off(ky, YB, os, os2)
+    long long os2;      // stride between y blocks (nx * YB * Zp)
     int ny, ncols, nchunks;
     Plan plan;
     const float2* tw;
@@ -43,6 +61,8 @@ struct XEnergyArgs {
     const float2* S;
     int L;
     long long rs, os;
+    int YB;
+    long long os2;
     int ny, ncols, nchunks, M;
     Plan plan;
     const float2* tw;
@@ -72,7 +92,14 @@ struct ZPassArgs {
     float scale;            // 1 / (ny nz)
     const double* cbar;     // FP64 mean (Z_STEP, Z_C2R); may be null (0)
     double* partials;       // bulk energy partial per CTA (Z_C2R) or null
+    // map_rows = 1: real rows rin / rout are a caller's C-order field; memory
+    // row r of the y-blocked spectrum is caller row x * ny + y
+    int map_rows, YB, nxr, nyr;
 };
+__host__ __device__ inline long long user_row(long long r, int YB, int nx, int ny) {
+    const long long x = (r / YB) % nx, yb = r / ((long long)YB * nx), yi = r % YB;
+    return x * ny + yb * YB + yi;
+}
 
 // launchers (evx_kernels.cu)
 cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st);

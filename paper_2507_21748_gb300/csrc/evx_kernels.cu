@@ -58,13 +58,14 @@ __global__ void __launch_bounds__(NT, 2) spass_kernel(SPassArgs a) {
     if (full) {
         for (int e = threadIdx.x; e < a.L * (SP / 2); e += NT) {
             const int i = e / (SP / 2), q = e % (SP / 2);
-            const float4 v = *reinterpret_cast<const float4*>(a.in + base + i * a.rs + 2 * q);
+            const float4 v = *reinterpret_cast<const float4*>(a.in + base + split_off(i, a.YB, a.rs, a.os2) + 2 * q);
             reinterpret_cast<float4*>(tile)[e] = v;
         }
     } else {
         for (int e = threadIdx.x; e < a.L * SP; e += NT) {
             const int i = e / SP, p = e % SP;
-            tile[e] = (col0 + p < a.ncols) ? a.in[base + i * a.rs + p] : make_float2(0.f, 0.f);
+            tile[e] = (col0 + p < a.ncols) ? a.in[base + split_off(i, a.YB, a.rs, a.os2) + p]
+                                           : make_float2(0.f, 0.f);
         }
     }
     __syncthreads();
@@ -72,13 +73,13 @@ __global__ void __launch_bounds__(NT, 2) spass_kernel(SPassArgs a) {
     if (full) {
         for (int e = threadIdx.x; e < a.L * (SP / 2); e += NT) {
             const int i = e / (SP / 2), q = e % (SP / 2);
-            *reinterpret_cast<float4*>(a.out + base + i * a.rs + 2 * q) =
+            *reinterpret_cast<float4*>(a.out + base + split_off(i, a.YB, a.rs, a.os2) + 2 * q) =
                 reinterpret_cast<const float4*>(tile)[e];
         }
     } else {
         for (int e = threadIdx.x; e < a.L * SP; e += NT) {
             const int i = e / SP, p = e % SP;
-            if (col0 + p < a.ncols) a.out[base + i * a.rs + p] = tile[e];
+            if (col0 + p < a.ncols) a.out[base + split_off(i, a.YB, a.rs, a.os2) + p] = tile[e];
         }
     }
 }
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(NT, 1) xupdate_kernel(XUpdArgs a) {
     for (int i = threadIdx.x; i < L; i += NT) tws[i] = a.tw[i];
     const int chunk = blockIdx.x, ky = blockIdx.y;
     const int col0 = chunk * SP;
-    const long long base = (long long)ky * a.os + col0;
+    const long long base = split_off(ky, a.YB, a.os, a.os2) + col0;
     const bool haveW = a.W != nullptr;
     if (haveW) load_x_cols(tile, 0, a.W, base, a.rs, L, col0, a.ncols);
     load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols);
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(NT, 1) xenergy_kernel(XEnergyArgs a) {
     for (int i = threadIdx.x; i < L; i += NT) tws[i] = a.tw[i];
     const int chunk = blockIdx.x, ky = blockIdx.y;
     const int col0 = chunk * SP;
-    const long long base = (long long)ky * a.os + col0;
+    const long long base = split_off(ky, a.YB, a.os, a.os2) + col0;
     load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols);
     __syncthreads();
     fft_cols<-1>(tile + SP, L, 2 * SP, a.plan, tws);
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
             const int r = e / M, n = e - r * M;
             float2 x = make_float2(0.f, 0.f);
             if (r < nr) {
-                x = reinterpret_cast<const float2*>(a.rin + (row0 + r) * a.rpitch)[n];
+                const long long rr = a.map_rows ? user_row(row0 + r, a.YB, a.nxr, a.nyr) : row0 + r;
+                x = reinterpret_cast<const float2*>(a.rin + rr * a.rpitch)[n];
                 x = make_float2((x.x - cb) - cbl, (x.y - cb) - cbl);
             }
             tile[r * PZ + n] = x;
@@ -270,8 +272,9 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
                     const float d0 = z.x * s, d1 = z.y * s;
                     tile[r * PZ + n] = make_float2(d0 * fmaf(d0, c3 + d0, gp), d1 * fmaf(d1, c3 + d1, gp));
                 } else {  // Z_C2R
+                    const long long rr = a.map_rows ? user_row(row0 + r, a.YB, a.nxr, a.nyr) : row0 + r;
                     if (a.rout)
-                        reinterpret_cast<float2*>(a.rout + (row0 + r) * a.rpitch)[n] = make_float2(c0, c1);
+                        reinterpret_cast<float2*>(a.rout + rr * a.rpitch)[n] = make_float2(c0, c1);
                     if (a.partials) {
                         const double q0 = (double)c0 * c0 - 1.0, q1 = (double)c1 * c1 - 1.0;
                         acc += q0 * q0 + q1 * q1;

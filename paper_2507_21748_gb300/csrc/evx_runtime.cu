@@ -120,7 +120,9 @@ SPassArgs y_args(const evx_grid* g, const float2* in, float2* out) {
     a.out = out;
     a.L = g->ny;
     a.rs = g->Zp;
-    a.os = (long long)g->ny * g->Zp;
+    a.os = (long long)g->YB * g->Zp;
+    a.YB = g->YB;
+    a.os2 = (long long)g->nx * g->YB * g->Zp;
     a.nouter = g->nx;
     a.ncols = g->M + 1;
     a.nchunks = g->Zp / SP;
@@ -136,8 +138,10 @@ XUpdArgs x_args(const evx_grid* g, const float2* W, float2* S, float2* S_out, do
     a.S = S;
     a.S_out = S_out;
     a.L = g->nx;
-    a.rs = (long long)g->ny * g->Zp;
+    a.rs = (long long)g->YB * g->Zp;
     a.os = g->Zp;
+    a.YB = g->YB;
+    a.os2 = (long long)g->nx * g->YB * g->Zp;
     a.ny = g->ny;
     a.ncols = g->M + 1;
     a.nchunks = g->Zp / SP;
@@ -163,6 +167,9 @@ ZPassArgs z_args(const evx_grid* g) {
     a.tw = g->twz;
     a.rtw = g->rtw;
     a.scale = (float)(1.0 / ((double)g->ny * g->nz));
+    a.YB = g->YB;
+    a.nxr = g->nx;
+    a.nyr = g->ny;
     return a;
 }
 
@@ -263,6 +270,7 @@ evx_status evx_grid_create(int nx, int ny, int nz, evx_params p, void* cuda_stre
     g->ny = ny;
     g->nz = nz;
     g->M = nz / 2;
+    g->YB = choose_yblock(ny, fast_paths_enabled());
     g->Zp = ((g->M + 1 + SP - 1) / SP) * SP;
     g->PZ = (g->M + 2) & ~1;
     g->zrows = TILE_CAP / g->PZ;
@@ -355,8 +363,9 @@ evx_status evx_set_stream(evx_grid* g, void* cuda_stream) {
 
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
-// real rows (pitch floats apart) -> spectral state S, FP64 mean -> d_scal[0]
-static evx_status load_real(evx_grid* g, const float* rows, long long pitch) {
+// real rows (pitch floats apart) -> spectral state S, FP64 mean -> d_scal[0].
+// map: rows are the caller's C-order field (else memory order of the spectrum)
+static evx_status load_real(evx_grid* g, const float* rows, long long pitch, int map) {
     const long long nrows = (long long)g->nx * g->ny;
     const double V = (double)nrows * g->nz;
     CK(launch_sum_field(rows, nrows, g->nz, pitch, g->d_part, SUM_BLOCKS, g->st));
@@ -364,6 +373,7 @@ static evx_status load_real(evx_grid* g, const float* rows, long long pitch) {
     ZPassArgs z = z_args(g);
     z.rin = rows;
     z.rpitch = pitch;
+    z.map_rows = map;
     z.out = g->W;
     z.cbar = g->d_scal;  // transform c - cbar
     CK(launch_zpass(z, Z_R2C, g->st));
@@ -377,28 +387,48 @@ static evx_status load_real(evx_grid* g, const float* rows, long long pitch) {
 evx_status evx_set_field(evx_grid* g, const float* d_c) {
     if (!g || !d_c) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!aligned8(d_c)) return fail(g, EVX_ERR_ARG, "field pointer must be 8-byte aligned");
-    return load_real(g, d_c, g->nz);
+    return load_real(g, d_c, g->nz, 1);
+}
+
+// copies between a caller's C-order real field (host) and real rows staged
+// in W's row slots (pitch 2 Zp floats) in the spectrum's memory row order:
+// one 3D copy per y block (rows (x, yi) of block yb)
+static evx_status host_rows_copy(evx_grid* g, float* host, bool to_device) {
+    const int nyb = g->ny / g->YB;
+    for (int yb = 0; yb < nyb; ++yb) {
+        cudaMemcpy3DParms c = {};
+        cudaPitchedPtr hp = make_cudaPitchedPtr(host + (size_t)yb * g->YB * g->nz, sizeof(float) * g->nz,
+                                                g->nz, g->ny);
+        cudaPitchedPtr dp = make_cudaPitchedPtr((float*)g->W + (size_t)yb * g->nx * g->YB * 2 * g->Zp,
+                                                sizeof(float) * 2 * g->Zp, g->nz, g->YB);
+        c.srcPtr = to_device ? hp : dp;
+        c.dstPtr = to_device ? dp : hp;
+        c.extent = make_cudaExtent(sizeof(float) * g->nz, g->YB, g->nx);
+        c.kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpy3DAsync(&c, g->st));
+    }
+    return EVX_OK;
 }
 
 evx_status evx_set_field_host(evx_grid* g, const float* h_c) {
     if (!g || !h_c) return fail(g, EVX_ERR_ARG, "NULL argument");
-    // stage real rows into the work buffer's row slots (pitch 2 Zp floats), then R2C in place
-    const long long nrows = (long long)g->nx * g->ny;
-    CK(cudaMemcpy2DAsync(g->W, sizeof(float) * 2 * g->Zp, h_c, sizeof(float) * g->nz,
-                         sizeof(float) * g->nz, nrows, cudaMemcpyHostToDevice, g->st));
-    evx_status s = load_real(g, (const float*)g->W, 2LL * g->Zp);
+    evx_status s = host_rows_copy(g, const_cast<float*>(h_c), true);
+    if (s != EVX_OK) return s;
+    s = load_real(g, (const float*)g->W, 2LL * g->Zp, 0);
     if (s != EVX_OK) return s;
     CK(cudaStreamSynchronize(g->st));
     return EVX_OK;
 }
 
-// state -> real rows (pitch floats apart), optional bulk-energy partials
-static evx_status store_real(evx_grid* g, float* rows, long long pitch, double* partials) {
+// state -> real rows (pitch floats apart), optional bulk-energy partials;
+// map as in load_real
+static evx_status store_real(evx_grid* g, float* rows, long long pitch, double* partials, int map) {
     CK(launch_spass(y_args(g, g->S, g->W), +1, g->st));
     ZPassArgs z = z_args(g);
     z.in = g->W;
     z.rout = rows;
     z.rpitch = pitch;
+    z.map_rows = map;
     z.cbar = g->d_scal;
     z.partials = partials;
     CK(launch_zpass(z, Z_C2R, g->st));
@@ -409,17 +439,16 @@ evx_status evx_get_field(evx_grid* g, float* d_out) {
     if (!g || !d_out) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     if (!aligned8(d_out)) return fail(g, EVX_ERR_ARG, "output pointer must be 8-byte aligned");
-    return store_real(g, d_out, g->nz, nullptr);
+    return store_real(g, d_out, g->nz, nullptr, 1);
 }
 
 evx_status evx_get_field_host(evx_grid* g, float* h_out) {
     if (!g || !h_out) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
-    evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, nullptr);
+    evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, nullptr, 0);
     if (s != EVX_OK) return s;
-    const long long nrows = (long long)g->nx * g->ny;
-    CK(cudaMemcpy2DAsync(h_out, sizeof(float) * g->nz, g->W, sizeof(float) * 2 * g->Zp,
-                         sizeof(float) * g->nz, nrows, cudaMemcpyDeviceToHost, g->st));
+    s = host_rows_copy(g, h_out, false);
+    if (s != EVX_OK) return s;
     CK(cudaStreamSynchronize(g->st));
     return check_timeouts(g);
 }
@@ -471,7 +500,7 @@ evx_status evx_energy(evx_grid* g, double* E, double* mass) {
     const double h3 = g->p.h * g->p.h * g->p.h;
     const double V = (double)g->nx * g->ny * g->nz;
     // bulk: h^3/4 sum (c^2-1)^2 over the real field (written into W's row slots, discarded)
-    evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, g->d_part);
+    evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, g->d_part, 0);
     if (s != EVX_OK) return s;
     ZPassArgs z = z_args(g);
     CK(launch_reduce_partials(g->d_part, zpass_grid(z), g->d_scal + 1, 0.25 * h3, g->st));
@@ -479,8 +508,10 @@ evx_status evx_energy(evx_grid* g, double* E, double* mass) {
     XEnergyArgs xa{};
     xa.S = g->S;
     xa.L = g->nx;
-    xa.rs = (long long)g->ny * g->Zp;
+    xa.rs = (long long)g->YB * g->Zp;
     xa.os = g->Zp;
+    xa.YB = g->YB;
+    xa.os2 = (long long)g->nx * g->YB * g->Zp;
     xa.ny = g->ny;
     xa.ncols = g->M + 1;
     xa.nchunks = g->Zp / SP;

@@ -115,6 +115,7 @@ extern "C" evx_status evx_ch_step_static(const float* d_c_in, float* d_c_out, in
     g.ny = ny;
     g.nz = nz;
     g.M = nz / 2;
+    g.YB = choose_yblock(ny, fast_paths_enabled());
     g.Zp = ((g.M + 1 + SP - 1) / SP) * SP;
     g.PZ = (g.M + 2) & ~1;
     g.zrows = std::max(1, TILE_CAP / g.PZ);
@@ -188,6 +189,7 @@ extern "C" evx_status evx_ch_step_static(const float* d_c_in, float* d_c_out, in
         ZPassArgs z = evxrt::z_args(&g);
         z.rin = d_c_in;
         z.rpitch = nz;
+        z.map_rows = 1;
         z.out = g.W;
         z.cbar = g.d_scal;
         CKS(launch_zpass(z, Z_R2C, st));
@@ -212,6 +214,7 @@ extern "C" evx_status evx_ch_step_static(const float* d_c_in, float* d_c_out, in
         z.in = g.W;
         z.rout = d_c_out;
         z.rpitch = nz;
+        z.map_rows = 1;
         z.cbar = g.d_scal;
         CKS(launch_zpass(z, Z_C2R, st));
     }

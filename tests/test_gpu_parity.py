@@ -178,9 +178,10 @@ def test_fast_and_generic_kernels_agree(evx, tmp_path):
     assert rel_l2(got, gen) <= 2e-6
 
 
-def test_host_io_matches_device_io(evx):
+@pytest.mark.parametrize("shape", [(32, 48, 40), (64, 128, 40), (24, 256, 64)])
+def test_host_io_matches_device_io(evx, shape):
+    """Host copies (per y block of the spectral layout) equal the device path."""
     import torch
-    shape = (32, 48, 40)
     c0 = inputs.uniform_field(shape, seed=5, offset=0.1)
     g = evx.Grid(shape)
     g.set_field_host(torch.from_numpy(c0))

@@ -33,12 +33,28 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// v[a] *= w_L^{+-n2 a}  (n2 ownership); tw is the shared-memory copy of the table
-template <int DIR>
-__device__ __forceinline__ void twiddle_a(float2 (&v)[32], int n2, const float2* tw) {
+// Twiddles of the four-step transform, re-indexed in shared memory so that
+// the threads of a warp read consecutive entries (no bank conflicts):
+//   tA[a * TP + n2]           = w_L^{n2 a}     (n2 ownership, a < 32)
+//   tB[(c * NB + i) * TP + j] = w_L^{a c}, a = j NB + i  (block ownership)
+// both filled from the L-entry table tw[m] = w_L^m at kernel start.
+template <int TP>
+__device__ __forceinline__ void fill_twiddles(float2* tA, float2* tB, const float2* __restrict__ tw, int nthreads) {
+    constexpr int NB = 32 / TP, L = 32 * TP;
+    for (int idx = threadIdx.x; idx < L; idx += nthreads) {
+        const int a = idx / TP, n2 = idx % TP;
+        tA[idx] = tw[n2 * a];
+        const int c = idx / 32, rem = idx % 32, i = rem / TP, j = rem % TP;
+        tB[idx] = tw[(j * NB + i) * c];
+    }
+}
+
+// v[a] *= w_L^{+-n2 a}  (n2 ownership)
+template <int TP, int DIR>
+__device__ __forceinline__ void twiddle_a(float2 (&v)[32], int n2, const float2* tA) {
 #pragma unroll
     for (int a = 1; a < 32; ++a) {
-        float2 w = tw[n2 * a];
+        float2 w = tA[a * TP + n2];
         if (DIR > 0) w.y = -w.y;
         v[a] = cmul(v[a], w);
     }
@@ -46,14 +62,13 @@ __device__ __forceinline__ void twiddle_a(float2 (&v)[32], int n2, const float2*
 
 // v[i TP + c] *= w_L^{+-a c}, a = j NB + i  (block ownership)
 template <int TP, int DIR>
-__device__ __forceinline__ void twiddle_b(float2 (&v)[32], int j, const float2* tw) {
+__device__ __forceinline__ void twiddle_b(float2 (&v)[32], int j, const float2* tB) {
     constexpr int NB = 32 / TP;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int a = j * NB + i;
 #pragma unroll
         for (int c = 1; c < TP; ++c) {
-            float2 w = tw[a * c];
+            float2 w = tB[(c * NB + i) * TP + j];
             if (DIR > 0) w.y = -w.y;
             v[i * TP + c] = cmul(v[i * TP + c], w);
         }
@@ -144,12 +159,13 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
     const int Zp = a.Zp, Zh = a.Zp / 2;
     float2* bin = reinterpret_cast<float2*>(smem4);  // [RPC][Zp]
     float2* xb = bin + RPC * Zp;                      // [RPC][RS]
-    float2* tws = xb + RPC * RS;                      // [M] complex FFT twiddles
-    float2* rtws = tws + M;                           // [M + 1] real-transform twiddles
+    float2* tA = xb + RPC * RS;                       // [M] complex FFT twiddles (n2 ownership)
+    float2* tB = tA + M;                              // [M] (block ownership)
+    float2* rtws = tB + M;                            // [M + 1] real-transform twiddles
     const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    for (int i = threadIdx.x; i < M; i += NTZ) tws[i] = a.tw[i];
+    fill_twiddles<TP>(tA, tB, a.tw, NTZ);
     for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
     auto issue = [&](int tl) {
         const long long row0 = (long long)tl * RPC;
@@ -190,7 +206,7 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
         if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
         // inverse complex FFT of length M
         Dft<32, 1>::run(v);
-        twiddle_a<1>(v, n2, tws);
+        twiddle_a<TP, 1>(v, n2, tA);
         t1_z<TP>(v, xb, n2, r);
         pass_b<TP, 1>(v);
         // real-space samples z[m] = c[2m] + i c[2m+1], m = k1 + 32 k2
@@ -211,7 +227,7 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
             }
         // forward complex FFT of length M from block ownership (m = a + 32 b)
         pass_b<TP, -1>(v);
-        twiddle_b<TP, -1>(v, n2, tws);
+        twiddle_b<TP, -1>(v, n2, tB);
         __syncthreads();
         t2_z<TP>(v, xb, n2, r);
         Dft<32, -1>::run(v);
@@ -308,13 +324,14 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
     extern __shared__ __align__(1024) float4 smem4[];
     float2* buf = reinterpret_cast<float2*>(smem4);  // [L][8] TMA destination
     float2* xb = buf + L * 8;                         // transpose, then store staging
-    float2* tws = xb + XB;                            // [L] twiddles
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tws + L);
+    float2* tA = xb + XB;                             // [L] twiddles (n2 ownership)
+    float2* tB = tA + L;                              // [L] twiddles (block ownership)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tB + L);
     const int p = threadIdx.x & 7, n2 = threadIdx.x >> 3;
     const int nchunks = a.nchunks;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    for (int i = threadIdx.x; i < L; i += 8 * TP) tws[i] = a.tw[i];
+    fill_twiddles<TP>(tA, tB, a.tw, 8 * TP);
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     auto issue = [&](int tl) {
@@ -341,7 +358,7 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
         const int next = tile + gridDim.x;
         if (threadIdx.x == 0 && next < ntiles) issue(next);
         Dft<32, DIR>::run(v);
-        twiddle_a<DIR>(v, n2, tws);
+        twiddle_a<TP, DIR>(v, n2, tA);
         t1_s<TP, 8>(v, xb, n2, p);
         pass_b<TP, DIR>(v);
         __syncthreads();  // transpose reads done: xb becomes the store staging tile
@@ -373,17 +390,16 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
     float2* bufW = reinterpret_cast<float2*>(smem4);
     float2* bufS = bufW + L * 8;
     float2* xb = bufS + L * 8;
-    float2* tws = xb + XB;
-    float* k2xs = reinterpret_cast<float*>(tws + L);
+    float2* tA = xb + XB;                                    // [L] twiddles (n2 ownership)
+    float2* tB = tA + L;                                     // [L] twiddles (block ownership)
+    float* k2xs = reinterpret_cast<float*>(tB + L);
     uint64_t* bars = reinterpret_cast<uint64_t*>(k2xs + L);  // [0] W, [1] S
     const int p = threadIdx.x & 7, n2 = threadIdx.x >> 3;
     const int nchunks = a.nchunks;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    for (int i = threadIdx.x; i < L; i += 8 * TP) {
-        tws[i] = a.tw[i];
-        k2xs[i] = a.k2x[i];
-    }
+    fill_twiddles<TP>(tA, tB, a.tw, 8 * TP);
+    for (int i = threadIdx.x; i < L; i += 8 * TP) k2xs[i] = a.k2x[i];
     if (threadIdx.x == 0) {
         mbar_init(bars + 0, 1);
         mbar_init(bars + 1, 1);
@@ -420,7 +436,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         __syncthreads();
         if (threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
         Dft<32, -1>::run(v);
-        twiddle_a<-1>(v, n2, tws);
+        twiddle_a<TP, -1>(v, n2, tA);
         t1_s<TP, 8>(v, xb, n2, p);
         pass_b<TP, -1>(v);
         const int kz = chunk * 8 + p;
@@ -446,7 +462,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         __syncthreads();
         if (threadIdx.x == 0 && next < ntiles) issue(&mS, bufS, bars + 1, next);
         Dft<32, -1>::run(v);
-        twiddle_a<-1>(v, n2, tws);
+        twiddle_a<TP, -1>(v, n2, tA);
         t1_s<TP, 8>(v, xb, n2, p);
         pass_b<TP, -1>(v);
         // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L; k = 0 stays out
@@ -461,7 +477,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         if (ky == 0 && kz == 0 && n2 == 0) v[0] = make_float2(0.f, 0.f);
         // ---- S' = F_x^-1 c_hat'
         pass_b<TP, 1>(v);
-        twiddle_b<TP, 1>(v, n2, tws);
+        twiddle_b<TP, 1>(v, n2, tB);
         __syncthreads();
         t2_s<TP, 8>(v, xb, n2, p);
         Dft<32, 1>::run(v);
@@ -588,7 +604,7 @@ static bool run_fspass_tma(const SPassArgs& a, cudaStream_t st, cudaError_t* err
     if (!make_map(&mi, a.in, a.ncols, 32, a.nouter, a.L, Zp, 32, 1, BOX / 32) ||
         !make_map(&mo, a.out, a.ncols, 32, a.nouter, a.L, Zp, 32, 1, BOX / 32))
         return false;
-    const size_t smem = sizeof(float2) * (L * 8 + (L + TP) * 8 + L) + 16;
+    const size_t smem = sizeof(float2) * (L * 8 + (L + TP) * 8 + 2 * L) + 16;
     int per = 0;
     cudaError_t e = prep(fast::fspass_tma_kernel<TP, DIR>, smem, 8 * TP, &per);
     if (e != cudaSuccess) {
@@ -613,7 +629,7 @@ static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) 
         !make_map(&ms, a.S, a.ncols, a.YB, a.L, a.ny, Zp, 1, BOX, 1) ||
         !make_map(&mo, a.S_out, a.ncols, a.YB, a.L, a.ny, Zp, 1, BOX, 1))
         return false;
-    const size_t smem = sizeof(float2) * (2 * L * 8 + (L + TP) * 8 + L) + sizeof(float) * L + 16;
+    const size_t smem = sizeof(float2) * (2 * L * 8 + (L + TP) * 8 + 2 * L) + sizeof(float) * L + 16;
     int per = 0;
     cudaError_t e = prep(fast::fxupd_tma_kernel<TP>, smem, 8 * TP, &per);
     if (e != cudaSuccess) {
@@ -657,7 +673,7 @@ template <int TP>
 static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st) {
     constexpr int NTZ = 128, RPC = NTZ / TP;
     const size_t smem =
-        sizeof(float2) * ((size_t)RPC * a.Zp + (size_t)RPC * (32 * TP + TP) + 32 * TP + 32 * TP + 1);
+        sizeof(float2) * ((size_t)RPC * a.Zp + (size_t)RPC * (32 * TP + TP) + 3 * 32 * TP + 1);
     int per = 0;
     cudaError_t e = prep(fast::fzstep_kernel<TP, NTZ>, smem, NTZ, &per);
     if (e != cudaSuccess) return e;

@@ -231,27 +231,26 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
         __syncthreads();
         t2_z<TP>(v, xb, n2, r);
         Dft<32, -1>::run(v);
-        // natural-order staging, then R2C post-processing in pairs (k, M - k)
-        __syncthreads();
+        // R2C post-processing from registers: thread n2 holds Z[n2 + TP d]; the
+        // partner Z[M - k] of k = n2 + TP d sits in thread TP - n2 at index
+        // 31 - d (thread 0: its own index 32 - d), fetched by warp shuffle.
+        //   X_k = (Z_k + conj Z_{M-k})/2 - i e^{-2 pi i k/nz} (Z_k - conj Z_{M-k})/2
+        const int lane = threadIdx.x & 31;
+        const int src = (lane & ~(TP - 1)) | ((TP - n2) & (TP - 1));
+        float2* out = a.out + row * Zp;
 #pragma unroll
-        for (int d = 0; d < 32; ++d) xb[r * RS + n2 + TP * d] = v[d];
-        __syncthreads();
-        for (int e = threadIdx.x; e < RPC * H; e += NTZ) {
-            const int rr = e / H, k = e - rr * H;
-            const long long orow = row0 + rr;
-            if (orow >= a.nrows) continue;
-            const int m = M - k;
-            const float2 zk = xb[rr * RS + k], zm = xb[rr * RS + (m == M ? 0 : m)];
+        for (int d = 0; d < 32; ++d) {
+            float2 zm;
+            zm.x = __shfl_sync(0xffffffffu, v[31 - d].x, src);
+            zm.y = __shfl_sync(0xffffffffu, v[31 - d].y, src);
+            if (n2 == 0) zm = v[(32 - d) & 31];
+            const float2 zk = v[d];
             const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
-            float2* out = a.out + orow * Zp;
-            out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
-            if (m != k) {
-                const float2 A2 = make_float2(A.x, -A.y);
-                const float2 B2 = make_float2(-B.x, B.y);
-                out[m] = cadd(A2, mul_i<-1>(cmul(rtws[m], B2)));
-            }
+            const int k = n2 + TP * d;
+            if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
         }
+        if (rowok && n2 == 0) out[M] = make_float2(v[0].x - v[0].y, 0.f);  // X_M = Re Z_0 - Im Z_0
     }
 }
 

@@ -92,14 +92,6 @@ __device__ __forceinline__ int slot_s(int n2, int a, int p) {
     constexpr int NB = 32 / TP;
     return (a * TP + n2 + a / NB) * P + p;
 }
-// Row tiles (one pencil per row r, row stride RS = M + TP): the same one-slot
-// padding per block of a staggers block-ownership accesses by 33 slots.
-template <int TP>
-__device__ __forceinline__ int slot_z(int r, int n2, int a) {
-    constexpr int NB = 32 / TP, RS = 32 * TP + TP;
-    return r * RS + a * TP + n2 + a / NB;
-}
-
 template <int TP, int P>
 __device__ __forceinline__ void t1_s(float2 (&v)[32], float2* xb, int n2, int p) {
     constexpr int NB = 32 / TP;
@@ -122,29 +114,6 @@ __device__ __forceinline__ void t2_s(float2 (&v)[32], float2* xb, int n2, int p)
 #pragma unroll
     for (int a = 0; a < 32; ++a) v[a] = xb[slot_s<TP, P>(n2, a, p)];
 }
-template <int TP>
-__device__ __forceinline__ void t1_z(float2 (&v)[32], float2* xb, int n2, int r) {
-    constexpr int NB = 32 / TP;
-#pragma unroll
-    for (int a = 0; a < 32; ++a) xb[slot_z<TP>(r, n2, a)] = v[a];
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-#pragma unroll
-        for (int c = 0; c < TP; ++c) v[i * TP + c] = xb[slot_z<TP>(r, c, n2 * NB + i)];
-}
-template <int TP>
-__device__ __forceinline__ void t2_z(float2 (&v)[32], float2* xb, int n2, int r) {
-    constexpr int NB = 32 / TP;
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-#pragma unroll
-        for (int c = 0; c < TP; ++c) xb[slot_z<TP>(r, c, n2 * NB + i)] = v[i * TP + c];
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 32; ++a) v[a] = xb[slot_z<TP>(r, n2, a)];
-}
-
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -153,13 +122,18 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // ------------------------------------------------ z pass: C2R, c^3 - c, R2C
 template <int TP, int NTZ>
-__global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int ntiles) {
-    constexpr int M = 32 * TP, NB = 32 / TP, RPC = NTZ / TP, RS = M + TP, H = M / 2 + 1;
+__global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int ntiles) {
+    constexpr int M = 32 * TP, NB = 32 / TP, RPC = NTZ / TP, RS = M + TP;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp, Zh = a.Zp / 2;
-    float2* bin = reinterpret_cast<float2*>(smem4);  // [RPC][Zp]
-    float2* xb = bin + RPC * Zp;                      // [RPC][RS]
-    float2* tA = xb + RPC * RS;                       // [M] complex FFT twiddles (n2 ownership)
+    // row stride of the shared tile: >= Zp and RS, and = TP (mod 16) so that the
+    // rows a warp spans fall on different banks
+    const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
+    // One tile buffer serves as cp.async destination (rows of Zp), transpose
+    // space (rows of RS) and is refilled for the next tile as soon as the last
+    // transpose has been read: 46 KB per CTA at M = 512, four CTAs per SM.
+    float2* buf = reinterpret_cast<float2*>(smem4);  // [RPC][BS]
+    float2* tA = buf + RPC * BS;                      // [M] complex FFT twiddles (n2 ownership)
     float2* tB = tA + M;                              // [M] (block ownership)
     float2* rtws = tB + M;                            // [M + 1] real-transform twiddles
     const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
@@ -173,7 +147,7 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
             const int rr = e / Zh, q = e - rr * Zh;
             const bool ok = row0 + rr < a.nrows;
             const float2* src = a.in + (row0 + rr) * Zp + 2 * q;
-            cp_async16(bin + rr * Zp + 2 * q, ok ? src : a.in, ok ? 16 : 0);
+            cp_async16(buf + rr * BS + 2 * q, ok ? src : a.in, ok ? 16 : 0);
         }
         cp_commit();
     };
@@ -184,6 +158,7 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
     const float gp = (float)(3.0 * cbd * cbd - 1.0);  // g'(cbar)
     const float c3 = (float)(3.0 * cbd);
     const float s = a.scale;
+    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB; };
     for (; tile < ntiles; tile += gridDim.x) {
         const long long row0 = (long long)tile * RPC;
         cp_wait<0>();
@@ -193,7 +168,7 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
 #pragma unroll
         for (int n1 = 0; n1 < 32; ++n1) {
             const int k = n2 + TP * n1;
-            float2 xk = bin[r * Zp + k], xm = bin[r * Zp + (M - k)];
+            float2 xk = buf[r * BS + k], xm = buf[r * BS + (M - k)];
             if (k == 0) {
                 xk.y = 0.f;
                 xm.y = 0.f;
@@ -202,12 +177,17 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
             const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);
             v[n1] = cadd(A, mul_i<1>(cmul(cconj(rtws[k]), B)));
         }
-        __syncthreads();
-        if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
+        __syncthreads();  // tile read: buf becomes transpose space
         // inverse complex FFT of length M
         Dft<32, 1>::run(v);
         twiddle_a<TP, 1>(v, n2, tA);
-        t1_z<TP>(v, xb, n2, r);
+#pragma unroll
+        for (int aa = 0; aa < 32; ++aa) buf[slot(r, n2, aa)] = v[aa];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) v[i * TP + c] = buf[slot(r, c, n2 * NB + i)];
         pass_b<TP, 1>(v);
         // real-space samples z[m] = c[2m] + i c[2m+1], m = k1 + 32 k2
         const long long row = row0 + r;
@@ -228,8 +208,16 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
         // forward complex FFT of length M from block ownership (m = a + 32 b)
         pass_b<TP, -1>(v);
         twiddle_b<TP, -1>(v, n2, tB);
+        __syncthreads();  // block-ownership reads of the first transpose done
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) buf[slot(r, c, n2 * NB + i)] = v[i * TP + c];
         __syncthreads();
-        t2_z<TP>(v, xb, n2, r);
+#pragma unroll
+        for (int aa = 0; aa < 32; ++aa) v[aa] = buf[slot(r, n2, aa)];
+        __syncthreads();  // buf free: fetch the next tile while this one finishes
+        if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
         Dft<32, -1>::run(v);
         // R2C post-processing from registers: thread n2 holds Z[n2 + TP d]; the
         // partner Z[M - k] of k = n2 + TP d sits in thread TP - n2 at index
@@ -253,7 +241,6 @@ __global__ void __launch_bounds__(NTZ, 256 / NTZ) fzstep_kernel(ZPassArgs a, int
         if (rowok && n2 == 0) out[M] = make_float2(v[0].x - v[0].y, 0.f);  // X_M = Re Z_0 - Im Z_0
     }
 }
-
 
 // ------------------------------------------------------------ TMA helpers
 // Tile loads and stores of the strided passes go through the tensor memory
@@ -670,9 +657,9 @@ bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
 
 template <int TP>
 static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st) {
-    constexpr int NTZ = 128, RPC = NTZ / TP;
-    const size_t smem =
-        sizeof(float2) * ((size_t)RPC * a.Zp + (size_t)RPC * (32 * TP + TP) + 3 * 32 * TP + 1);
+    constexpr int NTZ = 128, RPC = NTZ / TP, RS = 32 * TP + TP;
+    const int BS = TP + (((a.Zp > RS ? a.Zp : RS) - TP + 15) & ~15);  // as in the kernel
+    const size_t smem = sizeof(float2) * ((size_t)RPC * BS + 3 * 32 * TP + 1);
     int per = 0;
     cudaError_t e = prep(fast::fzstep_kernel<TP, NTZ>, smem, NTZ, &per);
     if (e != cudaSuccess) return e;

@@ -44,6 +44,30 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float) -> float:
+    """Largest x over the ranks of the default process group (x itself when not
+    distributed). NCCL groups reduce a CUDA tensor, others a CPU tensor."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size: int, steps: int, voxels: float, seconds: float) -> float:
+    """Whole-job voxel-steps/s: every rank advances its own replica of the field
+    (weak scaling), timed by the slowest rank."""
+    return world_size * steps * voxels / seconds
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of the initial field of replica ``rank`` (independent trajectories)."""
+    return rank
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -171,7 +195,7 @@ def main():
     n = args.n
     shape = (n, n, n)
     V = float(n) ** 3
-    c0 = inputs.uniform_field(shape, seed=rank, offset=0.3)
+    c0 = inputs.uniform_field(shape, seed=replica_seed(rank), offset=0.3)
     c0_dev = torch.from_numpy(c0).cuda()
     stream = torch.cuda.current_stream()
     g = evx.Grid(shape, dt=DT, M=MOB, kappa=KAPPA, h=H, stream=stream)
@@ -201,12 +225,8 @@ def main():
     ms = e0.elapsed_time(e1)
     pass_ms, pass_cnt = g.pass_times(reset=True)
     g.set_profiling(False)
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ws * args.steps * V / (t_max * 1e-3)
+    t_max = max_over_ranks(ms)
+    value = job_throughput(ws, args.steps, V, t_max * 1e-3)
 
     # roofline of the dominant pass
     names = ["x pass + k-space update", "y inverse", "z C2R + c^3-c + R2C", "y forward"]
@@ -234,12 +254,8 @@ def main():
         g.get_field_host(host_out)
         t1 = time.perf_counter()
         barrier()
-        te = t1 - t0
-        if ws > 1:
-            t = torch.tensor([te], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": ws * args.steps * V / te, "unit": UNIT,
+        te = max_over_ranks(t1 - t0)
+        e2e = {"value": job_throughput(ws, args.steps, V, te), "unit": UNIT,
                "h2d_bytes_per_step": 4.0 * V / args.steps, "d2h_bytes_per_step": 4.0 * V / args.steps,
                "job": "pinned host c0 -> evx_set_field_host -> %d steps -> evx_get_field_host; "
                       "the field's bytes are spread over the job's steps" % args.steps}

@@ -68,6 +68,23 @@ def replica_seed(rank: int) -> int:
     return rank
 
 
+def measured_traffic(dominant_pass: int, alg_bytes: float):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/traffic_x_pass.json: traffic / algorithmic bytes on a
+    smaller case), or None when that kernel's source has changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_x_pass.json")) as f:
+            d = json.load(f)
+        with open(os.path.join(ROOT, d["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except Exception:
+        return None
+    if dominant_pass != 0 or sha != d.get("source_sha256"):
+        return None
+    return d["traffic_over_algorithmic"] * alg_bytes
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -282,11 +299,13 @@ def main():
                                "M = kappa = 1, h = 1, %d steps" % (n, args.steps),
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%.2f GB per field vs 129 MB)" % (step_bytes / 9 / 1e9),
-                   "sweeps_per_step": step_bytes / (V * 4.0) if False else 9,
+                   "sweeps_per_step": 9,
                    "footprint_bytes": fp},
         "roofline": {"bound": "hbm", "kernel": kern[dom] + " (" + names[dom] + ")",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": peak_src + " hbm_gbs (copy)", "traffic": None,
+                     "peak_source": peak_src + " hbm_gbs (copy)",
+                     "traffic": measured_traffic(dom, alg_bytes),
+                     "traffic_source": "profiles/traffic_1024x1024x256.md (ratio scaled to this launch)",
                      "alg_bytes_per_launch": alg_bytes, "avg_ms": avg_ms,
                      "step_alg_bytes": step_bytes,
                      "step_effective_GBps": step_bytes / (t_max / args.steps * 1e-3) / 1e9,

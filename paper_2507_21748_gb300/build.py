@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libevx.so")
 SOURCES = ["evx_kernels.cu", "evx_fast.cu", "evx_runtime.cu", "evx_adjoint.cu", "evx_static.cu",
-           "evx_conv.cu"]
+           "evx_nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,7 +36,8 @@ def _deps_mtime():
     m = 0.0
     for fn in os.listdir(CSRC):
         m = max(m, os.path.getmtime(os.path.join(CSRC, fn)))
-    m = max(m, os.path.getmtime(os.path.join(HERE, "..", "include", "evx.h")))
+    for h in ("evx.h", "evx_nn.h"):
+        m = max(m, os.path.getmtime(os.path.join(HERE, "..", "include", h)))
     return m
 
 

@@ -1,0 +1,572 @@
+// Kernels of the learned surrogate: a 3D residual CNN that advances the
+// Cahn-Hilliard field by a block of solver steps. Periodic 3x3x3
+// convolutions as implicit GEMMs on the tensor cores (BF16 operands, FP32
+// accumulation, mma.sync m16n8k16), their data and weight gradients, and the
+// element-wise and reduction kernels of training (GELU, zero-mean output
+// correction, mean-squared loss, Adam) with FP64 reductions.
+//
+// Activations are BF16, channels-last: [B][X][Y][Z][C], C = 16 or 32.
+// Conv weights are [27][Cout][Cin] (tap t = 9 (dx+1) + 3 (dy+1) + (dz+1)),
+// Cin fastest; biases FP32 [Cout]. out(v, co) = b(co) + sum_t sum_ci
+// W[t][co][ci] in(v + off_t, ci) with periodic wrap.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "../../include/evx_nn.h"
+
+namespace evxnn {
+
+constexpr int TZ = 64;            // output voxels per tile row (along z)
+constexpr int TY = 2;             // tile rows (along y): a tile is 2 x 64 voxels
+constexpr int NTHR = 256;         // 8 warps x 16 voxels
+constexpr int HR = 3 * (TY + 2);  // halo rows: x - 1 .. x + 1, y0 - 1 .. y0 + TY
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t& r0, uint32_t& r1, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+// d gelu / dx = Phi(x) + x phi(x)
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+struct ConvArgs {
+    const __nv_bfloat16* in;     // [B][X][Y][Z][CIN]
+    const __nv_bfloat16* w;      // [27][COUT][CIN]
+    const float* bias;           // [COUT] or null
+    void* out;                   // bf16 [..][COUT] or f32 field
+    __nv_bfloat16* pre;          // GELU: pre-activation out; GELU_BWD: pre-activation in
+    const __nv_bfloat16* res;    // RESID: residual [..][COUT]
+    int B, X, Y, Z;
+    int ntiles;
+};
+
+// load the halo rows (x+dx, y0-1 .. y0+TY) x (z0-1 .. z0+TZ), periodic, into
+// s[HR][TZ+2][C+8] (pitch C+8 halves: conflict-free fragment loads); halo
+// row index (dx+1) * (TY+2) + (y - y0 + 1)
+template <int C>
+__device__ __forceinline__ void load_halo(__nv_bfloat16* s, const __nv_bfloat16* g, int b, int x, int y0, int z0,
+                                          int X, int Y, int Z, int nthreads) {
+    constexpr int P = C + 8, V16 = C / 8;  // 16-byte pieces per voxel
+    const int n = HR * (TZ + 2) * V16;
+    for (int e = threadIdx.x; e < n; e += nthreads) {
+        const int q = e % V16, rem = e / V16, zi = rem % (TZ + 2), nb = rem / (TZ + 2);
+        const int dx = nb / (TY + 2) - 1, yi = nb % (TY + 2) - 1;
+        const int xx = (x + dx + X) % X, yy = (y0 + yi + Y) % Y, zz = (z0 + zi - 1 + Z) % Z;
+        const long long vox = (((long long)b * X + xx) * Y + yy) * Z + zz;
+        const uint4 val = *reinterpret_cast<const uint4*>(g + vox * C + q * 8);
+        *reinterpret_cast<uint4*>(s + (nb * (TZ + 2) + zi) * P + q * 8) = val;
+    }
+}
+
+// tile index -> (b, x, y0, z0)
+__device__ __forceinline__ void tile_coords(int tile, int X, int Y, int Z, int& b, int& x, int& y0, int& z0) {
+    const int zt = Z / TZ, yt = Y / TY;
+    int r = tile;
+    z0 = (r % zt) * TZ;
+    r /= zt;
+    y0 = (r % yt) * TY;
+    r /= yt;
+    x = r % X;
+    b = r / X;
+}
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(NTHR) conv_fwd_kernel(ConvArgs a) {
+    constexpr int PI = CIN + 8, PW = CIN + 8, NT = COUT / 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem_raw);   // [27][COUT][PW]
+    __nv_bfloat16* sin = sw + 27 * COUT * PW;                          // [HR][TZ+2][PI]
+    for (int e = threadIdx.x; e < 27 * COUT * (CIN / 8); e += NTHR) {
+        const int q = e % (CIN / 8), row = e / (CIN / 8);
+        *reinterpret_cast<uint4*>(sw + row * PW + q * 8) = *reinterpret_cast<const uint4*>(a.w + row * CIN + q * 8);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+    const int yl = warp >> 2, zs = (warp & 3) * 16;  // warp's 16 voxels: row y0 + yl, z0 + zs ..
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        int b, x, y0, z0;
+        tile_coords(tile, a.X, a.Y, a.Z, b, x, y0, z0);
+        __syncthreads();  // previous tile done with sin (and weights loaded)
+        load_halo<CIN>(sin, a.in, b, x, y0, z0, a.X, a.Y, a.Z, NTHR);
+        __syncthreads();
+        float acc[NT][4];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+        const int zl = zs + g;
+#pragma unroll 1
+        for (int t = 0; t < 27; ++t) {
+            const int dx = t / 9, dy = (t / 3) % 3, dz = t % 3 - 1;
+            const int nb = dx * (TY + 2) + yl + dy;  // (dx+1)(TY+2) + (yl + (dy-1) + 1)
+            const __nv_bfloat16* r0 = sin + (nb * (TZ + 2) + zl + dz + 1) * PI;
+            const __nv_bfloat16* r1 = r0 + 8 * PI;
+            const __nv_bfloat16* wt = sw + t * COUT * PW;
+#pragma unroll
+            for (int ks = 0; ks < CIN / 16; ++ks) {
+                uint32_t af[4];
+                af[0] = *reinterpret_cast<const uint32_t*>(r0 + ks * 16 + 2 * tig);
+                af[1] = *reinterpret_cast<const uint32_t*>(r1 + ks * 16 + 2 * tig);
+                af[2] = *reinterpret_cast<const uint32_t*>(r0 + ks * 16 + 2 * tig + 8);
+                af[3] = *reinterpret_cast<const uint32_t*>(r1 + ks * 16 + 2 * tig + 8);
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const __nv_bfloat16* wr = wt + (nt * 8 + g) * PW + ks * 16 + 2 * tig;
+                    mma_bf16(acc[nt], af, *reinterpret_cast<const uint32_t*>(wr),
+                             *reinterpret_cast<const uint32_t*>(wr + 8));
+                }
+            }
+        }
+        // epilogue: rows g, g+8 of the warp's 16 voxels; columns co = nt*8 + 2 tig (+1)
+        const long long vbase = (((long long)b * a.X + x) * a.Y + y0 + yl) * a.Z + z0 + zs;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long vox = vbase + g + 8 * h;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int co = nt * 8 + 2 * tig;
+                float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+                if (a.bias) {
+                    v0 += a.bias[co];
+                    v1 += a.bias[co + 1];
+                }
+                const long long o = vox * COUT + co;
+                if (EPI == EVX_NN_EPI_FIELD) {
+                    if (co == 0) reinterpret_cast<float*>(a.out)[vox] = v0;
+                    continue;
+                }
+                if (EPI == EVX_NN_EPI_GELU) {
+                    *reinterpret_cast<__nv_bfloat162*>(a.pre + o) = __floats2bfloat162_rn(v0, v1);
+                    v0 = gelu(v0);
+                    v1 = gelu(v1);
+                } else if (EPI == EVX_NN_EPI_GELU_BWD) {
+                    const float2 p = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(a.pre + o));
+                    v0 *= gelu_grad(p.x);
+                    v1 *= gelu_grad(p.y);
+                } else if (EPI == EVX_NN_EPI_RESID) {
+                    const float2 q = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(a.res + o));
+                    v0 += q.x;
+                    v1 += q.y;
+                }
+                *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(a.out) + o) =
+                    __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- weight gradient
+// dW[t][co][ci] = sum_v dY(v, co) X(v + off_t, ci): per tap a (COUT x CIN) GEMM
+// over the voxels. Warp w owns accumulator tiles j = w, w + 4, ... of the
+// 27 * (COUT/16) * (CIN/8) m16n8 tiles; each CTA walks its voxel tiles and
+// writes its partial sums, reduced in a fixed order afterwards.
+struct WgradArgs {
+    const __nv_bfloat16* dy;   // [..][COUT]
+    const __nv_bfloat16* x;    // [..][CIN]
+    float* partials;           // [grid][27][COUT][CIN]
+    int B, X, Y, Z, ntiles;
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NTHR) conv_wgrad_kernel(WgradArgs a) {
+    constexpr int PI = CIN + 8, PD = COUT + 8, TPT = (COUT / 16) * (CIN / 8), NTOT = 27 * TPT;
+    constexpr int NW = NTHR / 32, MAXJ = (NTOT + NW - 1) / NW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16* sx = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // [HR][TZ+2][PI]
+    __nv_bfloat16* sdy = sx + HR * (TZ + 2) * PI;                     // [TY * TZ][PD]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+    float acc[MAXJ][4];
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        int b, x, y0, z0;
+        tile_coords(tile, a.X, a.Y, a.Z, b, x, y0, z0);
+        __syncthreads();
+        load_halo<CIN>(sx, a.x, b, x, y0, z0, a.X, a.Y, a.Z, NTHR);
+        for (int e = threadIdx.x; e < TY * TZ * (COUT / 8); e += NTHR) {
+            const int q = e % (COUT / 8), v = e / (COUT / 8), yl = v / TZ, z = v % TZ;
+            const long long vox = (((long long)b * a.X + x) * a.Y + y0 + yl) * a.Z + z0 + z;
+            *reinterpret_cast<uint4*>(sdy + v * PD + q * 8) =
+                *reinterpret_cast<const uint4*>(a.dy + vox * COUT + q * 8);
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int k0 = 0; k0 < TY * TZ; k0 += 16) {
+            const int yl = k0 / TZ, zk = k0 % TZ;  // the 16 voxels share a row
+#pragma unroll
+            for (int jj = 0; jj < MAXJ; ++jj) {
+                const int j = warp + NW * jj;
+                if (j < NTOT) {
+                    const int t = j / TPT, tile_ = j % TPT;
+                    const int mt = tile_ / (CIN / 8), nt = tile_ % (CIN / 8);
+                    // A = dY^T (co x v): 8x8 blocks (v 0-7 | 8-15) x (co 0-7 | 8-15), transposed
+                    uint32_t af[4];
+                    const int va = k0 + (lane & 7) + ((lane >> 4) << 3);
+                    ldsm_x4_trans(af, sdy + va * PD + mt * 16 + ((lane >> 3) & 1) * 8);
+                    // B = X shifted by tap t (v x ci): blocks v 0-7 and 8-15 of columns nt*8..+8
+                    const int dx = t / 9, dy = (t / 3) % 3, dz = t % 3 - 1;
+                    const int nb = dx * (TY + 2) + yl + dy;
+                    const int vb = zk + (lane & 7) + ((lane >> 3) & 1) * 8;
+                    uint32_t b0, b1;
+                    ldsm_x2_trans(b0, b1, sx + (nb * (TZ + 2) + vb + dz + 1) * PI + nt * 8);
+                    mma_bf16(acc[jj], af, b0, b1);
+                }
+            }
+        }
+    }
+    // write this CTA's partial dW (c0,c1: row g; c2,c3: row g+8; cols 2 tig, 2 tig + 1)
+    float* P = a.partials + (long long)blockIdx.x * 27 * COUT * CIN;
+#pragma unroll
+    for (int jj = 0; jj < MAXJ; ++jj) {
+        const int j = warp + NW * jj;
+        if (j < NTOT) {
+            const int t = j / TPT, tile_ = j % TPT;
+            const int mt = tile_ / (CIN / 8), nt = tile_ % (CIN / 8);
+            const int co = mt * 16 + g, ci = nt * 8 + 2 * tig;
+            float* p = P + ((long long)t * COUT + co) * CIN + ci;
+            p[0] = acc[jj][0];
+            p[1] = acc[jj][1];
+            p[8 * CIN] = acc[jj][2];
+            p[8 * CIN + 1] = acc[jj][3];
+        }
+    }
+}
+
+// out[i] = sum_b partials[b * n + i] in order b = 0, 1, ... (deterministic)
+__global__ void reduce_partials_f32(const float* partials, int nparts, int n, float* out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += partials[(long long)b * n + i];
+        out[i] = (float)s;
+    }
+}
+
+// ---------------------------------------------------------- element-wise
+// bias gradient: db[co] = sum_v dy(v, co); per-block FP64 partials
+__global__ void bias_grad_kernel(const __nv_bfloat16* dy, long long nvox, int C, double* partials) {
+    __shared__ double ws[256];
+    for (int co = 0; co < C; ++co) {
+        double s = 0.0;
+        for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+             v += (long long)gridDim.x * blockDim.x)
+            s += (double)__bfloat162float(dy[v * C + co]);
+        ws[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) ws[threadIdx.x] += ws[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partials[(long long)blockIdx.x * C + co] = ws[0];
+        __syncthreads();
+    }
+}
+__global__ void bias_grad_finish(const double* partials, int nparts, int C, float* db) {
+    const int co = threadIdx.x;
+    if (co < C) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += partials[b * C + co];
+        db[co] = (float)s;
+    }
+}
+
+// field (FP32, one value per voxel) -> activation with C channels, channel 0 = field * scale
+__global__ void field_to_act_kernel(const float* f, long long nvox, int C, float scale, __nv_bfloat16* act) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        for (int c = 0; c < C; ++c) act[v * C + c] = __float2bfloat16_rn(c == 0 ? f[v] * scale : 0.f);
+    }
+}
+
+// per-sample FP64 sums of a field: partials[s * nb + blk]
+__global__ void sample_sum_kernel(const float* f, long long V, double* partials, int nb) {
+    __shared__ double ws[256];
+    const int s = blockIdx.y;
+    double acc = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V;
+         v += (long long)gridDim.x * blockDim.x)
+        acc += (double)f[s * V + v];
+    ws[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) ws[threadIdx.x] += ws[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[s * nb + blockIdx.x] = ws[0];
+}
+
+// out = base + (d - mean_s(d)) per sample (base may be null: out = d - mean)
+__global__ void zero_mean_add_kernel(const float* base, const float* d, const double* partials, int nb, long long V,
+                                     float* out) {
+    const int s = blockIdx.y;
+    double m = 0.0;
+    for (int b = 0; b < nb; ++b) m += partials[s * nb + b];
+    const float mean = (float)(m / (double)V);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V;
+         v += (long long)gridDim.x * blockDim.x) {
+        const float x = d[s * V + v] - mean;
+        out[s * V + v] = base ? base[s * V + v] + x : x;
+    }
+}
+
+// squared error: partials of sum (p - t)^2 (FP64); grad = scale (p - t)
+__global__ void mse_kernel(const float* p, const float* t, long long n, float scale, float* grad, double* partials) {
+    __shared__ double ws[256];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float d = p[i] - t[i];
+        acc += (double)d * d;
+        if (grad) grad[i] = scale * d;
+    }
+    ws[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) ws[threadIdx.x] += ws[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = ws[0];
+}
+__global__ void sum_partials_kernel(const double* partials, int n, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += partials[i];
+        *out = s;
+    }
+}
+
+// dgrad weights: Wt[26 - t][ci][co] = W[t][co][ci] (BF16)
+__global__ void flip_weights_kernel(const __nv_bfloat16* w, int cout, int cin, __nv_bfloat16* wt) {
+    const int n = 27 * cout * cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = i % cin, co = (i / cin) % cout, t = i / (cin * cout);
+        wt[((26 - t) * cin + ci) * cout + co] = w[i];
+    }
+}
+
+// Adam on FP32 master parameters, BF16 copy refreshed (bf16 may be null)
+__global__ void adam_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                            float eps, float bc1, float bc2, __nv_bfloat16* wbf) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        w[i] = wi;
+        if (wbf) wbf[i] = __float2bfloat16_rn(wi);
+    }
+}
+
+__global__ void f32_to_bf16_kernel(const float* a, int n, __nv_bfloat16* b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16_rn(a[i]);
+}
+
+}  // namespace evxnn
+
+// ===================================================================== C-ABI
+using namespace evxnn;
+
+namespace {
+thread_local const char* g_nn_err = "";
+int g_nn_sms = 0;
+int nn_sms() {
+    if (!g_nn_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_nn_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_nn_sms <= 0) g_nn_sms = 1;
+    }
+    return g_nn_sms;
+}
+evx_status nn_fail(evx_status s, const char* m) {
+    g_nn_err = m;
+    return s;
+}
+evx_status nn_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return EVX_OK;
+    g_nn_err = cudaGetErrorString(e);
+    return EVX_ERR_CUDA;
+}
+bool dims_ok(int B, int X, int Y, int Z) {
+    return B > 0 && X > 0 && Y > 0 && Z > 0 && Z % TZ == 0 && Y % TY == 0;
+}
+
+template <int CIN, int COUT, int EPI>
+evx_status launch_conv(const ConvArgs& a0, cudaStream_t st) {
+    ConvArgs a = a0;
+    a.ntiles = a.B * a.X * (a.Y / TY) * (a.Z / TZ);
+    const size_t smem = sizeof(__nv_bfloat16) * (27 * COUT * (CIN + 8) + HR * (TZ + 2) * (CIN + 8));
+    cudaError_t e = cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT, EPI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return nn_cuda(e);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, conv_fwd_kernel<CIN, COUT, EPI>, NTHR, smem);
+    const int grid = std::min(a.ntiles, std::max(per, 1) * nn_sms());
+    conv_fwd_kernel<CIN, COUT, EPI><<<grid, NTHR, smem, st>>>(a);
+    return nn_cuda(cudaGetLastError());
+}
+
+template <int CIN, int COUT>
+evx_status conv_epi(int epi, const ConvArgs& a, cudaStream_t st) {
+    switch (epi) {
+        case EVX_NN_EPI_PLAIN: return launch_conv<CIN, COUT, EVX_NN_EPI_PLAIN>(a, st);
+        case EVX_NN_EPI_GELU: return launch_conv<CIN, COUT, EVX_NN_EPI_GELU>(a, st);
+        case EVX_NN_EPI_RESID: return launch_conv<CIN, COUT, EVX_NN_EPI_RESID>(a, st);
+        case EVX_NN_EPI_GELU_BWD: return launch_conv<CIN, COUT, EVX_NN_EPI_GELU_BWD>(a, st);
+        case EVX_NN_EPI_FIELD: return launch_conv<CIN, COUT, EVX_NN_EPI_FIELD>(a, st);
+    }
+    return nn_fail(EVX_ERR_ARG, "unknown epilogue");
+}
+
+template <int CIN, int COUT>
+evx_status launch_wgrad(const WgradArgs& a0, float* dw, float* partials, size_t partial_floats,
+                        cudaStream_t st) {
+    WgradArgs a = a0;
+    a.ntiles = a.B * a.X * (a.Y / TY) * (a.Z / TZ);
+    const size_t smem = sizeof(__nv_bfloat16) * (HR * (TZ + 2) * (CIN + 8) + TY * TZ * (COUT + 8));
+    cudaError_t e = cudaFuncSetAttribute(conv_wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return nn_cuda(e);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, conv_wgrad_kernel<CIN, COUT>, NTHR, smem);
+    const size_t per_cta = (size_t)27 * COUT * CIN;
+    int grid = std::min(a.ntiles, std::max(per, 1) * nn_sms());
+    grid = std::max(1, std::min(grid, (int)(partial_floats / per_cta)));
+    a.partials = partials;
+    conv_wgrad_kernel<CIN, COUT><<<grid, NTHR, smem, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return nn_cuda(e);
+    reduce_partials_f32<<<(int)((per_cta + 255) / 256), 256, 0, st>>>(partials, grid, (int)per_cta, dw);
+    return nn_cuda(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* evx_nn_last_error(void) { return g_nn_err; }
+
+evx_status evx_nn_conv3d(const void* in, const void* w, const float* bias, void* out, void* pre, const void* res,
+                         int B, int X, int Y, int Z, int cin, int cout, int epilogue, void* stream) {
+    if (!in || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
+    if (!dims_ok(B, X, Y, Z)) return nn_fail(EVX_ERR_SIZE, "need Y even and Z a multiple of 64");
+    if ((epilogue == EVX_NN_EPI_GELU || epilogue == EVX_NN_EPI_GELU_BWD) && !pre)
+        return nn_fail(EVX_ERR_ARG, "GELU epilogues need the pre-activation buffer");
+    if (epilogue == EVX_NN_EPI_RESID && !res) return nn_fail(EVX_ERR_ARG, "residual epilogue needs res");
+    ConvArgs a{};
+    a.in = (const __nv_bfloat16*)in;
+    a.w = (const __nv_bfloat16*)w;
+    a.bias = bias;
+    a.out = out;
+    a.pre = (__nv_bfloat16*)pre;
+    a.res = (const __nv_bfloat16*)res;
+    a.B = B;
+    a.X = X;
+    a.Y = Y;
+    a.Z = Z;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cin == 32 && cout == 32) return conv_epi<32, 32>(epilogue, a, st);
+    if (cin == 16 && cout == 32) return conv_epi<16, 32>(epilogue, a, st);
+    if (cin == 32 && cout == 16) return conv_epi<32, 16>(epilogue, a, st);
+    if (cin == 16 && cout == 16) return conv_epi<16, 16>(epilogue, a, st);
+    return nn_fail(EVX_ERR_ARG, "supported channel pairs: 16/32 -> 16/32");
+}
+
+evx_status evx_nn_conv3d_wgrad(const void* dy, const void* x, float* dw, float* partials, size_t partial_floats,
+                               int B, int X, int Y, int Z, int cin, int cout, void* stream) {
+    if (!dy || !x || !dw || !partials) return nn_fail(EVX_ERR_ARG, "NULL pointer");
+    if (!dims_ok(B, X, Y, Z)) return nn_fail(EVX_ERR_SIZE, "need Y even and Z a multiple of 64");
+    if (partial_floats < (size_t)27 * cin * cout) return nn_fail(EVX_ERR_ARG, "partials too small");
+    WgradArgs a{};
+    a.dy = (const __nv_bfloat16*)dy;
+    a.x = (const __nv_bfloat16*)x;
+    a.B = B;
+    a.X = X;
+    a.Y = Y;
+    a.Z = Z;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cin == 32 && cout == 32) return launch_wgrad<32, 32>(a, dw, partials, partial_floats, st);
+    if (cin == 16 && cout == 32) return launch_wgrad<16, 32>(a, dw, partials, partial_floats, st);
+    if (cin == 32 && cout == 16) return launch_wgrad<32, 16>(a, dw, partials, partial_floats, st);
+    if (cin == 16 && cout == 16) return launch_wgrad<16, 16>(a, dw, partials, partial_floats, st);
+    return nn_fail(EVX_ERR_ARG, "supported channel pairs: 16/32 -> 16/32");
+}
+
+evx_status evx_nn_bias_grad(const void* dy, long long nvox, int c, double* partials, int nparts, float* db,
+                            void* stream) {
+    if (!dy || !partials || !db || c <= 0 || c > 256 || nparts <= 0) return nn_fail(EVX_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    bias_grad_kernel<<<nparts, 256, 0, st>>>((const __nv_bfloat16*)dy, nvox, c, partials);
+    bias_grad_finish<<<1, 256, 0, st>>>(partials, nparts, c, db);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_flip_weights(const void* w, int cout, int cin, void* wt, void* stream) {
+    if (!w || !wt) return nn_fail(EVX_ERR_ARG, "NULL pointer");
+    flip_weights_kernel<<<64, 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)w, cout, cin,
+                                                               (__nv_bfloat16*)wt);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_field_to_act(const float* f, long long nvox, int c, float scale, void* act, void* stream) {
+    if (!f || !act || c <= 0) return nn_fail(EVX_ERR_ARG, "bad argument");
+    field_to_act_kernel<<<4 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(f, nvox, c, scale, (__nv_bfloat16*)act);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_zero_mean_add(const float* base, const float* d, int nsamples, long long V, double* partials,
+                                int nparts, float* out, void* stream) {
+    if (!d || !out || !partials || nsamples <= 0 || nparts <= 0 || nparts > 4096)
+        return nn_fail(EVX_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    sample_sum_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(d, V, partials, nparts);
+    zero_mean_add_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(base, d, partials, nparts, V, out);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_mse(const float* p, const float* t, long long n, float grad_scale, float* grad, double* partials,
+                      int nparts, double* d_sum, void* stream) {
+    if (!p || !t || !partials || !d_sum || nparts <= 0) return nn_fail(EVX_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    mse_kernel<<<nparts, 256, 0, st>>>(p, t, n, grad_scale, grad, partials);
+    sum_partials_kernel<<<1, 32, 0, st>>>(partials, nparts, d_sum);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_adam(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
+                       int step, void* wbf, void* stream) {
+    if (!w || !g || !m || !v || n <= 0 || step < 1) return nn_fail(EVX_ERR_ARG, "bad argument");
+    const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+    adam_kernel<<<std::min(4 * nn_sms(), (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        w, g, m, v, n, lr, b1, b2, eps, bc1, bc2, (__nv_bfloat16*)wbf);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_f32_to_bf16(const float* a, int n, void* b, void* stream) {
+    if (!a || !b || n <= 0) return nn_fail(EVX_ERR_ARG, "bad argument");
+    f32_to_bf16_kernel<<<std::min(4 * nn_sms(), (n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        a, n, (__nv_bfloat16*)b);
+    return nn_cuda(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,323 @@
+"""Learned surrogate of the semi-implicit Cahn-Hilliard step (binding + driver).
+
+A 3D residual CNN advances the field by a block of solver steps (C-ABI in
+include/evx_nn.h). Every forward, backward and optimiser step runs in
+libevx's kernels; PyTorch only provides device buffers. The plain solver
+generates the training pairs, serves as fallback when the surrogate's mass
+drift or energy increase exceeds a threshold, and judges its error.
+"""
+import ctypes
+import time
+
+import numpy as np
+import torch
+
+from . import evx, inputs
+
+lib = evx.lib
+NN_EXPORTS = ["evx_nn_conv3d", "evx_nn_conv3d_wgrad", "evx_nn_bias_grad", "evx_nn_flip_weights",
+              "evx_nn_field_to_act", "evx_nn_zero_mean_add", "evx_nn_mse", "evx_nn_adam",
+              "evx_nn_f32_to_bf16", "evx_nn_last_error"]
+EPI_PLAIN, EPI_GELU, EPI_RESID, EPI_GELU_BWD, EPI_FIELD = range(5)
+
+
+def _setup():
+    vp, i, ll, f, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_float, ctypes.c_int
+    sig = {
+        "evx_nn_conv3d": [vp, vp, vp, vp, vp, vp, i, i, i, i, i, i, i, vp],
+        "evx_nn_conv3d_wgrad": [vp, vp, vp, vp, ctypes.c_size_t, i, i, i, i, i, i, vp],
+        "evx_nn_bias_grad": [vp, ll, i, vp, i, vp, vp],
+        "evx_nn_flip_weights": [vp, i, i, vp, vp],
+        "evx_nn_field_to_act": [vp, ll, i, f, vp, vp],
+        "evx_nn_zero_mean_add": [vp, vp, i, ll, vp, i, vp, vp],
+        "evx_nn_mse": [vp, vp, ll, f, vp, vp, i, vp, vp],
+        "evx_nn_adam": [vp, vp, vp, vp, i, f, f, f, f, i, vp, vp],
+        "evx_nn_f32_to_bf16": [vp, i, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = st
+    lib.evx_nn_last_error.argtypes = []
+    lib.evx_nn_last_error.restype = ctypes.c_char_p
+
+
+_setup()
+
+
+def _p(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _ck(s):
+    if s != evx.EVX_OK:
+        raise evx.EvxError(s, lib.evx_nn_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Net:
+    """lift 1->W, nblocks x [conv W->W, GELU, conv W->W] + skip, projection W->1.
+
+    Parameters are FP32 masters with BF16 copies (and flipped BF16 copies for
+    the data gradients); activations BF16 channels-last for `batch` fields
+    of `shape`."""
+
+    CIN = 16  # the input field is padded to 16 channels (channel 0 = c)
+    CPROJ = 16  # the projection writes 16 channels, channel 0 is used
+
+    def __init__(self, shape, batch, width=32, nblocks=4, seed=0):
+        assert width == 32
+        self.shape, self.batch, self.W, self.nb = tuple(shape), int(batch), width, nblocks
+        self.V = int(np.prod(self.shape))
+        self.nvox = self.V * self.batch
+        dev = "cuda"
+        rng = np.random.default_rng(seed)
+
+        def w(co, ci, fan_in, gain):
+            return (rng.standard_normal((27, co, ci)) * gain * np.sqrt(2.0 / fan_in)).astype(np.float32)
+
+        W = self.W
+        init = [("W0", w(W, self.CIN, 27, 1.0)), ("b0", np.zeros(W, np.float32))]
+        for k in range(nblocks):
+            init += [("W1_%d" % k, w(W, W, 27 * W, 1.0)), ("b1_%d" % k, np.zeros(W, np.float32)),
+                     ("W2_%d" % k, w(W, W, 27 * W, 0.1)), ("b2_%d" % k, np.zeros(W, np.float32))]
+        wp = w(self.CPROJ, W, 27 * W, 0.01)
+        wp[:, 1:, :] = 0.0  # only channel 0 of the projection reaches the output
+        init += [("Wp", wp), ("bp", np.zeros(self.CPROJ, np.float32))]
+        w0 = init[0][1]
+        w0[:, :, 1:] = 0.0  # input channels 1.. are padding
+        self.names = [n for n, _ in init]
+        self.p = {n: torch.from_numpy(a).to(dev) for n, a in init}
+        self.g = {n: torch.zeros_like(t) for n, t in self.p.items()}
+        self.m = {n: torch.zeros_like(t) for n, t in self.p.items()}
+        self.v = {n: torch.zeros_like(t) for n, t in self.p.items()}
+        self.wbf = {n: torch.empty(t.shape, dtype=torch.bfloat16, device=dev)
+                    for n, t in self.p.items() if n.startswith("W")}
+        self.wflip = {n: torch.empty((27, t.shape[2], t.shape[1]), dtype=torch.bfloat16, device=dev)
+                      for n, t in self.p.items() if n.startswith("W") and n != "W0"}
+        self.step_count = 0
+        self._refresh_bf16()
+        bf = torch.bfloat16
+        nv = self.nvox
+        self.a_in = torch.empty((nv, self.CIN), dtype=bf, device=dev)
+        self.h = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks + 1)]
+        self.u = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks)]
+        self.a = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks)]
+        self.d = torch.empty(nv, dtype=torch.float32, device=dev)
+        self.pred = torch.empty(nv, dtype=torch.float32, device=dev)
+        self.gpred = torch.empty(nv, dtype=torch.float32, device=dev)
+        self.gact = torch.empty((nv, self.CPROJ), dtype=bf, device=dev)
+        self.dh = torch.empty((nv, W), dtype=bf, device=dev)
+        self.du = torch.empty((nv, W), dtype=bf, device=dev)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        self.partial_floats = 2 * sms * 27 * W * W
+        self.wpart = torch.empty(self.partial_floats, dtype=torch.float32, device=dev)
+        self.nparts = 2 * sms
+        self.dpart = torch.empty(self.nparts * max(W, self.batch), dtype=torch.float64, device=dev)
+        self.dsum = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    # ---------------------------------------------------------- parameters
+    def _refresh_bf16(self):
+        s = _stream()
+        for n, t in self.wbf.items():
+            _ck(lib.evx_nn_f32_to_bf16(_p(self.p[n]), self.p[n].numel(), _p(t), s))
+        for n, t in self.wflip.items():
+            co, ci = self.p[n].shape[1], self.p[n].shape[2]
+            _ck(lib.evx_nn_flip_weights(_p(self.wbf[n]), co, ci, _p(t), s))
+
+    def params_numpy(self):
+        """Parameters as the GPU uses them (BF16-rounded weights, FP32 biases), FP64."""
+        out = {}
+        for n, t in self.p.items():
+            if n in self.wbf:
+                out[n] = self.wbf[n].float().cpu().numpy().astype(np.float64)
+            else:
+                out[n] = t.cpu().numpy().astype(np.float64)
+        return {"W0": out["W0"], "b0": out["b0"], "Wp": out["Wp"], "bp": out["bp"],
+                "blocks": [(out["W1_%d" % k], out["b1_%d" % k], out["W2_%d" % k], out["b2_%d" % k])
+                           for k in range(self.nb)]}
+
+    # --------------------------------------------------------------- layers
+    def _conv(self, inp, wname, bias, out, cin, cout, epi, pre=None, res=None, flipped=False):
+        w = self.wflip[wname] if flipped else self.wbf[wname]
+        X, Y, Z = self.shape
+        _ck(lib.evx_nn_conv3d(_p(inp), _p(w), _p(bias), _p(out), _p(pre), _p(res), self.batch, X, Y, Z,
+                              cin, cout, epi, _stream()))
+
+    def _wgrad(self, dy, x, gname, cin, cout):
+        X, Y, Z = self.shape
+        _ck(lib.evx_nn_conv3d_wgrad(_p(dy), _p(x), _p(self.g[gname]), _p(self.wpart), self.partial_floats,
+                                    self.batch, X, Y, Z, cin, cout, _stream()))
+
+    def _bgrad(self, dy, gname, c):
+        _ck(lib.evx_nn_bias_grad(_p(dy), self.nvox, c, _p(self.dpart), self.nparts, _p(self.g[gname]),
+                                 _stream()))
+
+    # -------------------------------------------------------------- forward
+    def forward(self, c):
+        """c: float32 CUDA tensor (batch, X, Y, Z) -> c + zero-mean correction."""
+        assert c.is_contiguous() and c.numel() == self.nvox and c.dtype == torch.float32
+        self._c = c
+        s = _stream()
+        W = self.W
+        _ck(lib.evx_nn_field_to_act(_p(c), self.nvox, self.CIN, 1.0, _p(self.a_in), s))
+        self._conv(self.a_in, "W0", self.p["b0"], self.h[0], self.CIN, W, EPI_PLAIN)
+        for k in range(self.nb):
+            self._conv(self.h[k], "W1_%d" % k, self.p["b1_%d" % k], self.a[k], W, W, EPI_GELU, pre=self.u[k])
+            self._conv(self.a[k], "W2_%d" % k, self.p["b2_%d" % k], self.h[k + 1], W, W, EPI_RESID,
+                       res=self.h[k])
+        self._conv(self.h[self.nb], "Wp", self.p["bp"], self.d, W, self.CPROJ, EPI_FIELD)
+        _ck(lib.evx_nn_zero_mean_add(_p(c), _p(self.d), self.batch, self.V, _p(self.dpart), self.nparts,
+                                     _p(self.pred), s))
+        return self.pred.view(c.shape)
+
+    # ------------------------------------------------------------- backward
+    def loss(self, target):
+        """Mean squared error of the last forward vs target (FP64 sum on the GPU)."""
+        _ck(lib.evx_nn_mse(_p(self.pred), _p(target), self.nvox, 0.0, None, _p(self.dpart), self.nparts,
+                           _p(self.dsum), _stream()))
+        return float(self.dsum.item()) / self.nvox
+
+    def backward(self, target):
+        """Gradients of L = mean((pred - target)^2) into self.g; returns L."""
+        s = _stream()
+        W = self.W
+        _ck(lib.evx_nn_mse(_p(self.pred), _p(target), self.nvox, 2.0 / self.nvox, _p(self.gpred),
+                           _p(self.dpart), self.nparts, _p(self.dsum), s))
+        # transpose of the zero-mean projection is the projection itself
+        _ck(lib.evx_nn_zero_mean_add(None, _p(self.gpred), self.batch, self.V, _p(self.dpart), self.nparts,
+                                     _p(self.gpred), s))
+        _ck(lib.evx_nn_field_to_act(_p(self.gpred), self.nvox, self.CPROJ, 1.0, _p(self.gact), s))
+        self._wgrad(self.gact, self.h[self.nb], "Wp", W, self.CPROJ)
+        self._bgrad(self.gact, "bp", self.CPROJ)
+        self._conv(self.gact, "Wp", None, self.dh, self.CPROJ, W, EPI_PLAIN, flipped=True)
+        for k in range(self.nb - 1, -1, -1):
+            self._wgrad(self.dh, self.a[k], "W2_%d" % k, W, W)
+            self._bgrad(self.dh, "b2_%d" % k, W)
+            self._conv(self.dh, "W2_%d" % k, None, self.du, W, W, EPI_GELU_BWD, pre=self.u[k], flipped=True)
+            self._wgrad(self.du, self.h[k], "W1_%d" % k, W, W)
+            self._bgrad(self.du, "b1_%d" % k, W)
+            self._conv(self.du, "W1_%d" % k, None, self.dh, W, W, EPI_RESID, res=self.dh, flipped=True)
+        self._wgrad(self.dh, self.a_in, "W0", self.CIN, W)
+        self._bgrad(self.dh, "b0", W)
+        return float(self.dsum.item()) / self.nvox
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.step_count += 1
+        s = _stream()
+        for n in self.names:
+            _ck(lib.evx_nn_adam(_p(self.p[n]), _p(self.g[n]), _p(self.m[n]), _p(self.v[n]), self.p[n].numel(),
+                                lr, b1, b2, eps, self.step_count, None, s))
+        self._refresh_bf16()
+
+
+# ----------------------------------------------------------------- training
+class TrajectoryPool:
+    """B solver trajectories at `shape`, advanced `block` steps per draw; each
+    starts from c0 = mean(seed) + U(-0.05, 0.05) and is restarted with the next
+    seed after `horizon` steps (seeds cycle through first_seed .. last_seed)."""
+
+    def __init__(self, shape, batch, block=10, horizon=300, seeds=range(256), dt=0.1, M=1.0, kappa=1.0):
+        self.shape, self.batch, self.block, self.horizon = tuple(shape), batch, block, horizon
+        self.seeds = list(seeds)
+        self.next_seed = 0
+        self.grids = [evx.Grid(shape, dt=dt, M=M, kappa=kappa) for _ in range(batch)]
+        self.age = [0] * batch
+        self.cur = torch.empty((batch,) + self.shape, dtype=torch.float32, device="cuda")
+        self.nxt = torch.empty_like(self.cur)
+        for i in range(batch):
+            self._restart(i)
+
+    def _restart(self, i):
+        seed = self.seeds[self.next_seed % len(self.seeds)]
+        self.next_seed += 1
+        c0 = inputs.uniform_field(self.shape, seed=seed, offset=inputs.trajectory_mean(seed))
+        self.grids[i].set_field(torch.from_numpy(c0).cuda())
+        self.age[i] = 0
+
+    def draw(self):
+        """(c_n, c_{n+block}) for every trajectory of the pool."""
+        for i, g in enumerate(self.grids):
+            if self.age[i] >= self.horizon:
+                self._restart(i)
+            g.get_field(self.cur[i])
+            g.step(self.block)
+            g.get_field(self.nxt[i])
+            self.age[i] += self.block
+        return self.cur, self.nxt
+
+    def close(self):
+        for g in self.grids:
+            g.close()
+
+
+def train(net, pool, iters, lr=2e-3, lr_final=2e-4, log_every=50, log=None):
+    """Adam with a geometric learning-rate decay; returns the loss history."""
+    hist = []
+    for it in range(iters):
+        x, y = pool.draw()
+        net.forward(x.contiguous())
+        L = net.backward(y.contiguous())
+        frac = it / max(iters - 1, 1)
+        net.adam(lr * (lr_final / lr) ** frac)
+        hist.append(L)
+        if log and (it % log_every == 0 or it == iters - 1):
+            log("iter %5d loss %.4e" % (it, L))
+    return hist
+
+
+# -------------------------------------------------------- guarded rollout
+def rollout(net, c0, nblocks, block=10, dt=0.1, M=1.0, kappa=1.0, mass_tol=1e-6, energy_tol=1e-7):
+    """Advance c0 (batch, X, Y, Z) by nblocks x block steps with the surrogate;
+    a sample whose predicted block drifts in mass beyond mass_tol (relative
+    to its L1 norm) or raises the energy beyond energy_tol (relative) is
+    recomputed by the plain solver for that block. Returns (fields, stats)."""
+    shape = tuple(c0.shape[1:])
+    B = c0.shape[0]
+    judge = evx.Grid(shape, dt=dt, M=M, kappa=kappa)
+    c = c0.clone()
+    fallbacks = 0
+    t_net = t_guard = t_fb = 0.0
+    for _ in range(nblocks):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pred = net.forward(c.contiguous()).clone()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        t_net += t1 - t0
+        for i in range(B):
+            judge.set_field(c[i])
+            E0, m0 = judge.energy()
+            l1 = float(c[i].abs().double().sum())
+            judge.set_field(pred[i])
+            E1, m1 = judge.energy()
+            ok = abs(m1 - m0) <= mass_tol * l1 and E1 <= E0 * (1 + energy_tol) + 1e-300
+            t2 = time.perf_counter()
+            if not ok:
+                judge.set_field(c[i])
+                judge.step(block)
+                judge.get_field(pred[i])
+                fallbacks += 1
+                torch.cuda.synchronize()
+                t_fb += time.perf_counter() - t2
+        t_guard += time.perf_counter() - t1
+        c = pred
+    judge.close()
+    return c, {"fallbacks": fallbacks, "blocks": nblocks * B, "t_net_s": t_net, "t_guard_s": t_guard - t_fb,
+               "t_fallback_s": t_fb}
+
+
+def solver_run(c0, nsteps, dt=0.1, M=1.0, kappa=1.0):
+    """Plain-solver reference for a batch of fields."""
+    shape = tuple(c0.shape[1:])
+    g = evx.Grid(shape, dt=dt, M=M, kappa=kappa)
+    out = torch.empty_like(c0)
+    for i in range(c0.shape[0]):
+        g.set_field(c0[i].contiguous())
+        g.step(nsteps)
+        g.get_field(out[i])
+    g.close()
+    return out

@@ -8,7 +8,7 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "evx.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("evx.h", "evx_nn.h")]
 
 
 @pytest.fixture(scope="module")
@@ -19,9 +19,11 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(evx_\w+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(evx_\w+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_entry_points():
@@ -37,7 +39,8 @@ def test_exports_every_declared_symbol(lib):
 
 def test_binding_lists_every_declared_symbol():
     import paper_2507_21748_gb300.evx as evx
-    assert sorted(evx.EXPORTS) == declared_functions()
+    import paper_2507_21748_gb300.surrogate as sur
+    assert sorted(evx.EXPORTS + sur.NN_EXPORTS) == declared_functions()
 
 
 class Params(ctypes.Structure):

@@ -1,0 +1,216 @@
+"""GPU kernels of the learned surrogate against the FP64 oracle (oracle/nn.py).
+
+Inputs and weights are rounded to BF16 once and given to both sides, so the
+comparison measures the kernels (FP32 accumulation, BF16 outputs), not the
+input rounding."""
+import numpy as np
+import pytest
+
+from oracle import nn as N
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_21748_gb300 import surrogate
+    return surrogate
+
+
+def bf16(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+SHAPE = (2, 4, 6, 64)  # B, X, Y, Z
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16), (16, 16)])
+@pytest.mark.parametrize("epi", [0, 1, 2, 3, 4])
+def test_conv_forward_epilogues(S, cin, cout, epi):
+    import torch
+    rng = np.random.default_rng(cin * 100 + cout + epi)
+    x = bf16(rng.standard_normal(SHAPE + (cin,)))
+    w = bf16(rng.standard_normal((27, cout, cin)) * 0.1)
+    b = torch.from_numpy(rng.standard_normal(cout).astype(np.float32))
+    pre = bf16(rng.standard_normal(SHAPE + (cout,)))
+    res = bf16(rng.standard_normal(SHAPE + (cout,)))
+    xd, wd, bd, pred_, resd = x.cuda(), w.cuda(), b.cuda(), pre.cuda(), res.cuda()
+    if epi == 4:
+        out = torch.empty(SHAPE, dtype=torch.float32, device="cuda")
+    else:
+        out = torch.empty(SHAPE + (cout,), dtype=torch.bfloat16, device="cuda")
+    B, X, Y, Z = SHAPE
+    S._ck(S.lib.evx_nn_conv3d(S._p(xd), S._p(wd), S._p(bd), S._p(out), S._p(pred_), S._p(resd),
+                              B, X, Y, Z, cin, cout, epi, S._stream()))
+    torch.cuda.synchronize()
+    ref = N.conv(x.float().numpy().astype(np.float64), w.float().numpy().astype(np.float64),
+                 b.numpy().astype(np.float64))
+    got = out.float().cpu().numpy()
+    if epi == 4:
+        assert rel(got, ref[..., 0]) < 1e-5
+        return
+    if epi == 1:
+        assert rel(pred_.float().cpu().numpy(), ref) < 8e-3
+        ref = N.gelu(ref)
+    elif epi == 2:
+        ref = ref + res.float().numpy()
+    elif epi == 3:
+        ref = ref * N.gelu_grad(pre.float().numpy().astype(np.float64))
+    assert rel(got, ref) < 8e-3  # BF16 output rounding (2^-9 relative)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16)])
+def test_conv_dgrad_and_wgrad(S, cin, cout):
+    import torch
+    rng = np.random.default_rng(7 + cin + cout)
+    x = bf16(rng.standard_normal(SHAPE + (cin,)))
+    dy = bf16(rng.standard_normal(SHAPE + (cout,)))
+    w = bf16(rng.standard_normal((27, cout, cin)) * 0.1)
+    B, X, Y, Z = SHAPE
+    xd, dyd, wd = x.cuda(), dy.cuda(), w.cuda()
+    wt = torch.empty((27, cin, cout), dtype=torch.bfloat16, device="cuda")
+    S._ck(S.lib.evx_nn_flip_weights(S._p(wd), cout, cin, S._p(wt), S._stream()))
+    dx = torch.empty(SHAPE + (cin,), dtype=torch.bfloat16, device="cuda")
+    S._ck(S.lib.evx_nn_conv3d(S._p(dyd), S._p(wt), None, S._p(dx), None, None, B, X, Y, Z, cout, cin, 0,
+                              S._stream()))
+    dw = torch.empty((27, cout, cin), dtype=torch.float32, device="cuda")
+    part = torch.empty(64 * 27 * cin * cout, dtype=torch.float32, device="cuda")
+    S._ck(S.lib.evx_nn_conv3d_wgrad(S._p(dyd), S._p(xd), S._p(dw), S._p(part), part.numel(), B, X, Y, Z, cin,
+                                    cout, S._stream()))
+    torch.cuda.synchronize()
+    xn, dyn, wn = (t.float().numpy().astype(np.float64) for t in (x, dy, w))
+    assert rel(dx.float().cpu().numpy(), N.conv_dgrad(dyn, wn)) < 8e-3
+    assert rel(dw.cpu().numpy(), N.conv_wgrad(dyn, xn)) < 1e-5
+
+
+def test_network_forward_and_gradients_vs_oracle(S):
+    import torch
+    shape, B = (6, 4, 64), 2
+    net = S.Net(shape, B, seed=3)
+    # a net whose blocks do something: larger second convs and projection
+    rng = np.random.default_rng(4)
+    for n in net.names:
+        if n.startswith("W2_") or n == "Wp":
+            net.p[n].mul_(10.0 if n != "Wp" else 30.0)
+        if n.startswith("b"):
+            net.p[n].copy_(torch.from_numpy(rng.standard_normal(net.p[n].shape).astype(np.float32) * 0.05))
+    net.p["Wp"][:, 1:, :] = 0
+    net.p["bp"][1:] = 0
+    net._refresh_bf16()
+    c = rng.uniform(-0.4, 0.4, (B,) + shape).astype(np.float32)
+    t = (c + rng.normal(0, 0.05, c.shape)).astype(np.float32)
+    cd, td = torch.from_numpy(c).cuda(), torch.from_numpy(t).cuda()
+    pred = net.forward(cd).clone()
+    L = net.backward(td)
+    torch.cuda.synchronize()
+    P = net.params_numpy()
+    Lr, pr, gr = N.loss_and_grads(P, c.astype(np.float64), t.astype(np.float64))
+    assert rel(pred.cpu().numpy() - c, pr - c) < 2e-2
+    assert abs(L - Lr) < 2e-2 * Lr
+    # mass: the correction is zero-mean per sample (FP64 mean, FP32 field)
+    drift = np.abs((pred.cpu().numpy().astype(np.float64) - c).sum(axis=(1, 2, 3)))
+    assert drift.max() < 1e-6 * np.abs(c).sum(axis=(1, 2, 3)).min()
+    flat = {"W0": gr["W0"], "b0": gr["b0"], "Wp": gr["Wp"], "bp": gr["bp"]}
+    for k, (dW1, db1, dW2, db2) in enumerate(gr["blocks"]):
+        flat.update({"W1_%d" % k: dW1, "b1_%d" % k: db1, "W2_%d" % k: dW2, "b2_%d" % k: db2})
+    scale = max(float(np.abs(r).max()) for r in flat.values())
+    for n, ref in flat.items():
+        got = net.g[n].cpu().numpy().astype(np.float64)
+        if n in ("Wp", "bp"):
+            got, ref = got[:, :1] if n == "Wp" else got[:1], ref[:, :1] if n == "Wp" else ref[:1]
+        if n == "W0":
+            got, ref = got[..., :1], ref[..., :1]
+        if np.abs(ref).max() < 1e-9 * scale:
+            # a parameter that only adds a constant to the correction (the projection
+            # bias, the last block's output bias): zero-mean output makes its exact
+            # gradient 0; the GPU returns the rounding noise of a BF16 sum
+            assert np.abs(got).max() < 1e-3 * scale, n
+            continue
+        cos = float(np.sum(got * ref) / (np.linalg.norm(got) * np.linalg.norm(ref) + 1e-300))
+        assert cos > 0.999 and rel(got, ref) < 5e-2, (n, cos, rel(got, ref))
+
+
+def test_training_beats_persistence_and_untrained(S):
+    """The trained surrogate (solver-generated pairs, 10 steps per block) predicts
+    held-out 10-step blocks better than c_{n+10} = c_n and than its initial state."""
+    import torch
+    shape, B = (32, 32, 64), 4
+    pool = S.TrajectoryPool(shape, B, block=10, horizon=100, seeds=range(0, 64))
+    net = S.Net(shape, B, seed=0)
+    held = S.TrajectoryPool(shape, B, block=10, horizon=100, seeds=range(200, 204))
+    xs, ys = [], []
+    for _ in range(5):
+        x, y = held.draw()
+        xs.append(x.clone())
+        ys.append(y.clone())
+
+    def err(n):
+        e = []
+        for x, y in zip(xs, ys):
+            p = n.forward(x.contiguous())
+            e.append(float(((p - y) ** 2).sum() / ((y - y.mean()) ** 2).sum()) ** 0.5)
+        return float(np.mean(e))
+
+    persist = float(np.mean([float(((x - y) ** 2).sum() / ((y - y.mean()) ** 2).sum()) ** 0.5
+                             for x, y in zip(xs, ys)]))
+    e0 = err(net)
+    hist = S.train(net, pool, 300, lr=2e-3, lr_final=2e-4)
+    e1 = err(net)
+    pool.close()
+    held.close()
+    assert hist[-1] < 0.2 * hist[0]
+    assert e1 < 0.5 * persist and e1 < 0.5 * e0, (e1, persist, e0)
+
+
+class _Perturbed:
+    """Stand-in surrogate for testing the guards: c + a fixed perturbation."""
+
+    def __init__(self, kind, shape, B):
+        import torch
+        g = torch.Generator(device="cuda").manual_seed(5)
+        if kind == "noise":  # large independent noise: raises the energy
+            self.delta = 0.5 * torch.randn((B,) + shape, generator=g, device="cuda")
+            self.delta -= self.delta.mean(dim=(1, 2, 3), keepdim=True)
+        else:  # a constant: changes the mass
+            self.delta = torch.full((B,) + shape, 1e-3, device="cuda")
+
+    def forward(self, c):
+        return c + self.delta
+
+
+@pytest.mark.parametrize("kind", ["noise", "mass"])
+def test_guarded_rollout_falls_back(S, kind):
+    """A block whose prediction raises the energy or moves the mass is recomputed by
+    the solver, so such a rollout equals the plain solver run (up to the FP32
+    round trip of the field between blocks)."""
+    import torch
+    from paper_2507_21748_gb300 import inputs
+    shape, B = (16, 16, 64), 2
+    c0 = torch.stack([torch.from_numpy(inputs.uniform_field(shape, seed=s, offset=0.2)) for s in range(B)]).cuda()
+    out, st = S.rollout(_Perturbed(kind, shape, B), c0, nblocks=3)
+    ref = S.solver_run(c0, 30)
+    assert st["fallbacks"] == st["blocks"] == 6
+    assert rel(out.cpu().numpy(), ref.cpu().numpy().astype(np.float64)) < 1e-5
+
+
+def test_guarded_rollout_accepts_the_solver_itself(S):
+    """A stand-in that returns the solver's own block passes both guards."""
+    import torch
+    from paper_2507_21748_gb300 import inputs
+    shape, B = (16, 16, 64), 2
+
+    class Exact:
+        def forward(self, c):
+            return S.solver_run(c.contiguous(), 10)
+
+    c0 = torch.stack([torch.from_numpy(inputs.uniform_field(shape, seed=s)) for s in range(B)]).cuda()
+    out, st = S.rollout(Exact(), c0, nblocks=2)
+    assert st["fallbacks"] == 0

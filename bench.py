@@ -18,6 +18,8 @@ voxel-steps / max time over ranks.
 """
 import argparse
 import json
+
+import numpy as np
 import os
 import subprocess
 import sys
@@ -41,6 +43,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1024, help="grid edge (default 1024)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--train-iters", type=int, default=200)
     return ap.parse_args()
 
 
@@ -167,6 +171,91 @@ def cpu_baseline_oracle(n_sample=256, steps=2):
                       "at 1024^3 it would be no faster" % (steps, n_sample, dt)}
 
 
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def surrogate_bench(args):
+    """Learned surrogate (10 solver steps per block): train at 128^3 on solver
+    trajectories (seeds 0..255, mean in [-0.3, 0.3], noise 0.05), then advance 8
+    fields of 256^3 by 3 blocks with the guarded surrogate and with the plain
+    solver; report times, the surrogate's error judged by the solver and the
+    conv kernel's tensor throughput."""
+    import torch
+    from paper_2507_21748_gb300 import evx, inputs
+    from paper_2507_21748_gb300 import surrogate as S
+    out = {}
+    tr_shape, B = (128, 128, 128), 4
+    pool = S.TrajectoryPool(tr_shape, B, block=10, horizon=30, seeds=range(256))
+    net = S.Net(tr_shape, B, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = S.train(net, pool, args.train_iters, lr=2e-3, lr_final=2e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out["train"] = {"grid": "128^3", "batch": B, "iters": args.train_iters, "pairs": B * args.train_iters,
+                    "trajectories": min(256, pool.next_seed), "seconds": t_train,
+                    "loss_first": hist[0], "loss_last": float(np.mean(hist[-10:]))}
+    pool.close()
+    shape, NB, blocks = (256, 256, 256), 8, 3
+    inf = S.Net(shape, NB, train=False)
+    inf.load_params(net)
+    del net
+    seeds = range(1000, 1000 + NB)
+    c0 = torch.stack([torch.from_numpy(inputs.uniform_field(shape, seed=s, offset=inputs.trajectory_mean(s)))
+                      for s in seeds]).cuda()
+    # plain solver: 8 fields x 30 steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ref = S.solver_run(c0, 10 * blocks)
+    torch.cuda.synchronize()
+    t_solver = time.perf_counter() - t0
+    # surrogate + guards + fallback
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got, st = S.rollout(inf, c0, blocks)
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t0
+    d = (got.double() - ref.double()).flatten(1)
+    r = ref.double().flatten(1)
+    rel = float((d.norm(dim=1) / r.norm(dim=1)).max())
+    persist = float(((c0.double() - ref.double()).flatten(1).norm(dim=1) / r.norm(dim=1)).max())
+    out["inference"] = {"grid": "256^3", "batch": NB, "blocks_per_field": blocks, "steps_per_block": 10,
+                        "t_solver_s": t_solver, "t_surrogate_path_s": t_sur,
+                        "speedup_vs_solver": t_solver / t_sur, "rel_l2_vs_solver_max": rel,
+                        "rel_l2_persistence_max": persist, "meets_1e-2": rel <= 1e-2,
+                        "block_evaluations": st["blocks"], "fallbacks": st["fallbacks"],
+                        "t_net_s": st["t_net_s"], "t_guard_s": st["t_guard_s"],
+                        "t_fallback_s": st["t_fallback_s"]}
+    # conv 32 -> 32 throughput at 256^3 x 8 (dominant surrogate kernel)
+    X, Y, Z = shape
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        inf._conv(inf.h[0], "W1_0", inf.p["b1_0"], inf.a[0], 32, 32, S.EPI_GELU, pre=inf.u[0])
+    e0.record()
+    reps = 5
+    for _ in range(reps):
+        inf._conv(inf.h[0], "W1_0", inf.p["b1_0"], inf.a[0], 32, 32, S.EPI_GELU, pre=inf.u[0])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * 27 * 32 * 32 * NB * X * Y * Z
+    peak, src = bf16_peak()
+    out["conv_roofline"] = {"bound": "tensor", "kernel": "conv_fwd_kernel<32,32,GELU> (mma.sync bf16)",
+                            "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                            "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_source": src + " bf16_tflops",
+                            "ms_per_launch": ms}
+    del inf
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
@@ -279,6 +368,14 @@ def main():
         del host_in, host_out
     fp = g.footprint()
     g.close()
+    del c0_dev
+    torch.cuda.empty_cache()
+    sur = None
+    if not args.no_surrogate and args.n == 1024:
+        try:
+            sur = surrogate_bench(args)
+        except Exception as ex:  # report, do not fail the bench
+            sur = {"error": repr(ex)}
 
     if rank != 0:
         if ws > 1:
@@ -314,6 +411,7 @@ def main():
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": 4 * args.steps,
+        "surrogate": sur,
     }
     print(json.dumps(out), flush=True)
     if ws > 1:

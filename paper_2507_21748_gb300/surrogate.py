@@ -68,9 +68,10 @@ class Net:
     CIN = 16  # the input field is padded to 16 channels (channel 0 = c)
     CPROJ = 16  # the projection writes 16 channels, channel 0 is used
 
-    def __init__(self, shape, batch, width=32, nblocks=4, seed=0):
+    def __init__(self, shape, batch, width=32, nblocks=4, seed=0, train=True):
         assert width == 32
         self.shape, self.batch, self.W, self.nb = tuple(shape), int(batch), width, nblocks
+        self.training = train
         self.V = int(np.prod(self.shape))
         self.nvox = self.V * self.batch
         dev = "cuda"
@@ -103,6 +104,16 @@ class Net:
         bf = torch.bfloat16
         nv = self.nvox
         self.a_in = torch.empty((nv, self.CIN), dtype=bf, device=dev)
+        if not train:
+            # inference: the residual stream is updated in place; one GELU input/output pair
+            h, u, a = (torch.empty((nv, W), dtype=bf, device=dev) for _ in range(3))
+            self.h, self.u, self.a = [h] * (nblocks + 1), [u] * nblocks, [a] * nblocks
+            self.d = torch.empty(nv, dtype=torch.float32, device=dev)
+            self.pred = torch.empty(nv, dtype=torch.float32, device=dev)
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            self.nparts = 2 * sms
+            self.dpart = torch.empty(self.nparts * max(W, self.batch), dtype=torch.float64, device=dev)
+            return
         self.h = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks + 1)]
         self.u = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks)]
         self.a = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks)]
@@ -127,6 +138,12 @@ class Net:
         for n, t in self.wflip.items():
             co, ci = self.p[n].shape[1], self.p[n].shape[2]
             _ck(lib.evx_nn_flip_weights(_p(self.wbf[n]), co, ci, _p(t), s))
+
+    def load_params(self, other):
+        """Take the parameters of another Net (e.g. trained at another size)."""
+        for n in self.names:
+            self.p[n].copy_(other.p[n])
+        self._refresh_bf16()
 
     def params_numpy(self):
         """Parameters as the GPU uses them (BF16-rounded weights, FP32 biases), FP64."""
@@ -183,6 +200,7 @@ class Net:
 
     def backward(self, target):
         """Gradients of L = mean((pred - target)^2) into self.g; returns L."""
+        assert self.training, "inference-only Net"
         s = _stream()
         W = self.W
         _ck(lib.evx_nn_mse(_p(self.pred), _p(target), self.nvox, 2.0 / self.nvox, _p(self.gpred),

@@ -84,6 +84,19 @@ evx_status evx_nn_adam(float *w, const float *g, float *m, float *v, int n, floa
 /* BF16 copy of an FP32 array. */
 evx_status evx_nn_f32_to_bf16(const float *a, int n, void *b, void *stream);
 
+/* Convolution engines for the 32 -> 32 layers (Z a multiple of 64):
+ * TCGEN05 (default) issues tcgen05.mma from shared-memory operands into a
+ * tensor-memory accumulator; MMA_SYNC uses warp-level mma.sync fragments.
+ * Other channel pairs always use MMA_SYNC. Process-wide setting. */
+enum { EVX_NN_ENGINE_TCGEN05 = 0, EVX_NN_ENGINE_MMA_SYNC = 1 };
+evx_status evx_nn_set_conv_engine(int engine);
+int evx_nn_conv_engine(void);
+
+/* Synchronizes the device and reports whether a tensor-core pipeline wait
+ * ran past its bound since the last check (EVX_ERR_CUDA; the flag is then
+ * cleared). Such a kernel returns early and leaves its outputs invalid. */
+evx_status evx_nn_check(void);
+
 /* Message of the last failed evx_nn_* call of this thread. */
 const char *evx_nn_last_error(void);
 

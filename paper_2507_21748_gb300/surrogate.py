@@ -17,8 +17,10 @@ from . import evx, inputs
 lib = evx.lib
 NN_EXPORTS = ["evx_nn_conv3d", "evx_nn_conv3d_wgrad", "evx_nn_bias_grad", "evx_nn_flip_weights",
               "evx_nn_field_to_act", "evx_nn_zero_mean_add", "evx_nn_mse", "evx_nn_adam",
-              "evx_nn_f32_to_bf16", "evx_nn_last_error"]
+              "evx_nn_f32_to_bf16", "evx_nn_set_conv_engine", "evx_nn_conv_engine", "evx_nn_check",
+              "evx_nn_last_error"]
 EPI_PLAIN, EPI_GELU, EPI_RESID, EPI_GELU_BWD, EPI_FIELD = range(5)
+ENGINE_TCGEN05, ENGINE_MMA_SYNC = 0, 1
 
 
 def _setup():
@@ -33,6 +35,9 @@ def _setup():
         "evx_nn_mse": [vp, vp, ll, f, vp, vp, i, vp, vp],
         "evx_nn_adam": [vp, vp, vp, vp, i, f, f, f, f, i, vp, vp],
         "evx_nn_f32_to_bf16": [vp, i, vp, vp],
+        "evx_nn_set_conv_engine": [i],
+        "evx_nn_conv_engine": [],
+        "evx_nn_check": [],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -52,6 +57,20 @@ def _p(t):
 def _ck(s):
     if s != evx.EVX_OK:
         raise evx.EvxError(s, lib.evx_nn_last_error().decode())
+
+
+def set_conv_engine(engine):
+    """ENGINE_TCGEN05 (default) or ENGINE_MMA_SYNC for the 32 -> 32 convolutions."""
+    _ck(lib.evx_nn_set_conv_engine(engine))
+
+
+def conv_engine():
+    return lib.evx_nn_conv_engine()
+
+
+def check():
+    """Synchronize and raise if a tensor-core pipeline wait ran past its bound."""
+    _ck(lib.evx_nn_check())
 
 
 def _stream():

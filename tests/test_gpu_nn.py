@@ -67,6 +67,63 @@ def test_conv_forward_epilogues(S, cin, cout, epi):
     assert rel(got, ref) < 8e-3  # BF16 output rounding (2^-9 relative)
 
 
+def _conv32(S, engine, shape, epi, seed):
+    import torch
+    rng = np.random.default_rng(seed)
+    x = bf16(rng.standard_normal(shape + (32,)))
+    w = bf16(rng.standard_normal((27, 32, 32)) * 0.1)
+    b = torch.from_numpy(rng.standard_normal(32).astype(np.float32))
+    pre = bf16(rng.standard_normal(shape + (32,)))
+    res = bf16(rng.standard_normal(shape + (32,)))
+    xd, wd, bd, pred_, resd = x.cuda(), w.cuda(), b.cuda(), pre.cuda(), res.cuda()  # held until the check
+    out = torch.empty(shape + (32,), dtype=torch.bfloat16, device="cuda")
+    B, X, Y, Z = shape
+    S.set_conv_engine(engine)
+    try:
+        S._ck(S.lib.evx_nn_conv3d(S._p(xd), S._p(wd), S._p(bd), S._p(out), S._p(pred_), S._p(resd),
+                                  B, X, Y, Z, 32, 32, epi, S._stream()))
+        S.check()
+    finally:
+        S.set_conv_engine(S.ENGINE_TCGEN05)
+    ref = N.conv(x.float().numpy().astype(np.float64), w.float().numpy().astype(np.float64),
+                 b.numpy().astype(np.float64))
+    if epi == 1:
+        assert rel(pred_.float().cpu().numpy(), ref) < 8e-3
+        ref = N.gelu(ref)
+    elif epi == 2:
+        ref = ref + res.float().numpy()
+    elif epi == 3:
+        ref = ref * N.gelu_grad(pre.float().numpy().astype(np.float64))
+    return out.float().cpu().numpy(), ref
+
+
+@pytest.mark.parametrize("shape", [(1, 3, 4, 64), (2, 2, 2, 128), (1, 5, 6, 192), (1, 1, 2, 64)])
+@pytest.mark.parametrize("epi", [0, 1, 2, 3])
+def test_conv32_engines_agree_with_oracle(S, shape, epi):
+    """32 -> 32 convolution on the tcgen05 engine and on the mma.sync engine:
+    both within BF16 output rounding of the FP64 oracle, and within a few BF16
+    ulps of each other (same BF16 operands, FP32 accumulation in another order);
+    X = 1 and Y = 2 make every periodic neighbour wrap onto the tile itself."""
+    seed = sum(shape) * 10 + epi
+    got_tc, ref = _conv32(S, S.ENGINE_TCGEN05, shape, epi, seed)
+    got_ms, _ = _conv32(S, S.ENGINE_MMA_SYNC, shape, epi, seed)
+    assert rel(got_tc, ref) < 8e-3
+    assert rel(got_ms, ref) < 8e-3
+    assert rel(got_tc, got_ms) < 8e-3
+    assert np.max(np.abs(got_tc - ref)) < 0.05 * np.max(np.abs(ref)) + 0.05
+
+
+def test_conv_engine_setting(S):
+    import paper_2507_21748_gb300.evx as evx
+    assert S.conv_engine() == S.ENGINE_TCGEN05
+    with pytest.raises(evx.EvxError):
+        S.set_conv_engine(7)
+    S.set_conv_engine(S.ENGINE_MMA_SYNC)
+    assert S.conv_engine() == S.ENGINE_MMA_SYNC
+    S.set_conv_engine(S.ENGINE_TCGEN05)
+    S.check()
+
+
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16)])
 def test_conv_dgrad_and_wgrad(S, cin, cout):
     import torch

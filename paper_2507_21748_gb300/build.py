@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libevx.so")
 SOURCES = ["evx_kernels.cu", "evx_fast.cu", "evx_runtime.cu", "evx_adjoint.cu", "evx_static.cu",
-           "evx_nn.cu"]
+           "evx_nn.cu", "evx_nn_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -15,13 +15,9 @@
 #include <cstdint>
 
 #include "../../include/evx_nn.h"
+#include "evx_nn_common.cuh"
 
 namespace evxnn {
-
-constexpr int TZ = 64;            // output voxels per tile row (along z)
-constexpr int TY = 2;             // tile rows (along y): a tile is 2 x 64 voxels
-constexpr int NTHR = 256;         // 8 warps x 16 voxels
-constexpr int HR = 3 * (TY + 2);  // halo rows: x - 1 .. x + 1, y0 - 1 .. y0 + TY
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
@@ -31,9 +27,6 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void* p) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -46,22 +39,6 @@ __device__ __forceinline__ void ldsm_x2_trans(uint32_t& r0, uint32_t& r1, const 
                  : "r"(smem_addr(p)));
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
-// d gelu / dx = Phi(x) + x phi(x)
-__device__ __forceinline__ float gelu_grad(float x) {
-    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
-}
-
-struct ConvArgs {
-    const __nv_bfloat16* in;     // [B][X][Y][Z][CIN]
-    const __nv_bfloat16* w;      // [27][COUT][CIN]
-    const float* bias;           // [COUT] or null
-    void* out;                   // bf16 [..][COUT] or f32 field
-    __nv_bfloat16* pre;          // GELU: pre-activation out; GELU_BWD: pre-activation in
-    const __nv_bfloat16* res;    // RESID: residual [..][COUT]
-    int B, X, Y, Z;
-    int ntiles;
-};
 
 // load the halo rows (x+dx, y0-1 .. y0+TY) x (z0-1 .. z0+TZ), periodic, into
 // s[HR][TZ+2][C+8] (pitch C+8 halves: conflict-free fragment loads); halo
@@ -81,17 +58,6 @@ __device__ __forceinline__ void load_halo(__nv_bfloat16* s, const __nv_bfloat16*
     }
 }
 
-// tile index -> (b, x, y0, z0)
-__device__ __forceinline__ void tile_coords(int tile, int X, int Y, int Z, int& b, int& x, int& y0, int& z0) {
-    const int zt = Z / TZ, yt = Y / TY;
-    int r = tile;
-    z0 = (r % zt) * TZ;
-    r /= zt;
-    y0 = (r % yt) * TY;
-    r /= yt;
-    x = r % X;
-    b = r / X;
-}
 
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(NTHR) conv_fwd_kernel(ConvArgs a) {
@@ -175,202 +141,6 @@ __global__ void __launch_bounds__(NTHR) conv_fwd_kernel(ConvArgs a) {
     }
 }
 
-
-// ------------------------------------------------ tcgen05 convolution 32 -> 32
-// Implicit GEMM on the 5th-generation tensor cores: per tile of 128 output
-// voxels (2 rows x 64 z) D[128 x 32] (FP32, tensor memory) accumulates
-// 27 taps x 2 K-steps of A[128 x 16] (BF16 activations) times B[16 x 32]
-// (BF16 weights). Operands sit in shared memory in the no-swizzle K-major
-// core-matrix layout (8 rows x 16 bytes per 128-byte core matrix): weights as
-// [t][co/8][ci/8][8][8], the halo as three copies shifted by dz = -1, 0, +1 so
-// that every tap's A operand starts on an 8-voxel boundary:
-// [dz][halo row][v/8][ci/8][8][8]. Core matrices adjacent along K are 128 B
-// apart (leading byte offset), along M/N 512 B (stride byte offset).
-// One thread issues the MMAs, the commit arrives on an mbarrier (bounded
-// wait), and each of the 4 warps reads its 32 accumulator lanes (one voxel
-// row each) with tcgen05.ld for the fused epilogue.
-__device__ int g_tc_timeout;
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version (sm_100 family); no swizzle, base offset 0
-    return d;
-}
-
-// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N, M
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > (1LL << 32)) return false;
-    }
-}
-
-template <int EPI>
-__global__ void __launch_bounds__(128, 1) conv_tc_kernel(ConvArgs a) {
-    constexpr int C = 32, HALO = HR * 8 * 4 * 128;  // bytes per dz copy
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* swb = smem_raw;                          // weights: 27 * 4 * 4 * 128 B
-    unsigned char* shalo = smem_raw + 27 * 4 * 4 * 128;     // 3 copies of HALO bytes
-    uint64_t* bar = reinterpret_cast<uint64_t*>(shalo + 3 * HALO);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // weights -> core-matrix layout
-    for (int e = threadIdx.x; e < 27 * C * 4; e += 128) {  // 16-byte pieces: (t, co, cig)
-        const int cig = e & 3, co = (e >> 2) % C, t = e / (4 * C);
-        const uint4 v = *reinterpret_cast<const uint4*>(a.w + ((long long)t * C + co) * C + cig * 8);
-        *reinterpret_cast<uint4*>(swb + (((t * 4 + (co >> 3)) * 4 + cig) * 8 + (co & 7)) * 16) = v;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_addr(tslot))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-    constexpr uint32_t IDESC = idesc_bf16(128, 32);
-    uint32_t parity = 0;
-    bool failed = false;
-    for (int tile = blockIdx.x; tile < a.ntiles && !failed; tile += gridDim.x) {
-        int b, x, y0, z0;
-        tile_coords(tile, a.X, a.Y, a.Z, b, x, y0, z0);
-        // halo -> three dz-shifted copies in core-matrix layout
-        for (int e = threadIdx.x; e < HR * (TZ + 2) * 4; e += 128) {
-            const int cig = e & 3, rem = e >> 2, zi = rem % (TZ + 2), nb = rem / (TZ + 2);
-            const int dx = nb / (TY + 2) - 1, yi = nb % (TY + 2) - 1;
-            const int xx = (x + dx + a.X) % a.X, yy = (y0 + yi + a.Y) % a.Y, zz = (z0 + zi - 1 + a.Z) % a.Z;
-            const long long vox = (((long long)b * a.X + xx) * a.Y + yy) * a.Z + zz;
-            const uint4 v = *reinterpret_cast<const uint4*>(a.in + vox * C + cig * 8);
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {  // copy s holds position p = zi - s (dz = s - 1)
-                const int p = zi - s;
-                if (p >= 0 && p < TZ)
-                    *reinterpret_cast<uint4*>(shalo + s * HALO + (((nb * 8 + (p >> 3)) * 4 + cig) * 8 + (p & 7)) * 16) =
-                        v;
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (threadIdx.x == 0) {
-            const uint32_t hbase = smem_addr(shalo), wbase = smem_addr(swb);
-            int k = 0;
-            for (int t = 0; t < 27; ++t) {
-                const int dxi = t / 9, dyi = (t / 3) % 3, s = t % 3;
-                const int nb0 = dxi * (TY + 2) + dyi;  // halo row of the first output row (yl = 0)
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks, ++k) {
-                    const uint64_t ad = sdesc(hbase + s * HALO + ((nb0 * 8) * 4 + 2 * ks) * 128, 128, 512);
-                    const uint64_t bd = sdesc(wbase + (t * 16 + 2 * ks) * 128, 128, 512);
-                    tc_mma(tmem, ad, bd, IDESC, k > 0);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(bar))
-                         : "memory");
-        }
-        const bool ok = tc_wait(smem_addr(bar), parity);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        parity ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: thread = accumulator lane = voxel m of the tile (m < 64: row y0, else y0 + 1)
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int m = warp * 32 + lane;
-        const long long vox = (((long long)b * a.X + x) * a.Y + y0 + (m >> 6)) * a.Z + z0 + (m & 63);
-        const long long o = vox * C;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {  // 8 channels per 16-byte store
-            float v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[q * 8 + j]) + (a.bias ? a.bias[q * 8 + j] : 0.f);
-            uint4 outw;
-            __nv_bfloat162* ow = reinterpret_cast<__nv_bfloat162*>(&outw);
-            if (EPI == EVX_NN_EPI_GELU) {
-                uint4 pw;
-                __nv_bfloat162* pp = reinterpret_cast<__nv_bfloat162*>(&pw);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    pp[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                    ow[j] = __floats2bfloat162_rn(gelu(v[2 * j]), gelu(v[2 * j + 1]));
-                }
-                *reinterpret_cast<uint4*>(a.pre + o + q * 8) = pw;
-            } else if (EPI == EVX_NN_EPI_GELU_BWD) {
-                const uint4 pw = *reinterpret_cast<const uint4*>(a.pre + o + q * 8);
-                const __nv_bfloat162* pp = reinterpret_cast<const __nv_bfloat162*>(&pw);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float2 pf = __bfloat1622float2(pp[j]);
-                    ow[j] = __floats2bfloat162_rn(v[2 * j] * gelu_grad(pf.x), v[2 * j + 1] * gelu_grad(pf.y));
-                }
-            } else if (EPI == EVX_NN_EPI_RESID) {
-                const uint4 rw = *reinterpret_cast<const uint4*>(a.res + o + q * 8);
-                const __nv_bfloat162* rp = reinterpret_cast<const __nv_bfloat162*>(&rw);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float2 rf = __bfloat1622float2(rp[j]);
-                    ow[j] = __floats2bfloat162_rn(v[2 * j] + rf.x, v[2 * j + 1] + rf.y);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) ow[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-            }
-            *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + o + q * 8) = outw;
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // accumulator read before the next tile's MMAs overwrite it
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    if (failed && threadIdx.x == 0) {
-        atomicExch(&g_tc_timeout, 1);
-        tc_wait(smem_addr(bar), parity);  // let the outstanding commit land (bounded) before freeing TMEM
-    }
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
-}
 
 // ----------------------------------------------------------- weight gradient
 // dW[t][co][ci] = sum_v dY(v, co) X(v + off_t, ci): per tap a (COUT x CIN) GEMM
@@ -613,21 +383,9 @@ bool dims_ok(int B, int X, int Y, int Z) {
 std::atomic<int> g_engine{EVX_NN_ENGINE_TCGEN05};
 bool use_tcgen05() { return g_engine.load() == EVX_NN_ENGINE_TCGEN05; }
 
-template <int EPI>
-evx_status launch_conv_tc(const ConvArgs& a0, cudaStream_t st) {
-    ConvArgs a = a0;
-    a.ntiles = a.B * a.X * (a.Y / TY) * (a.Z / TZ);
-    const size_t smem = 27 * 4 * 4 * 128 + 3 * (size_t)HR * 8 * 4 * 128 + 16;
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return nn_cuda(e);
-    const int grid = std::min(a.ntiles, nn_sms());
-    conv_tc_kernel<EPI><<<grid, 128, smem, st>>>(a);
-    return nn_cuda(cudaGetLastError());
-}
-
 template <int CIN, int COUT, int EPI>
 evx_status launch_conv(const ConvArgs& a0, cudaStream_t st) {
-    if (CIN == 32 && COUT == 32 && EPI != EVX_NN_EPI_FIELD && use_tcgen05()) return launch_conv_tc<EPI>(a0, st);
+    if (CIN == 32 && COUT == 32 && EPI != EVX_NN_EPI_FIELD && use_tcgen05()) return nn_cuda(conv32_tc(a0, EPI, st, nn_sms()));
     ConvArgs a = a0;
     a.ntiles = a.B * a.X * (a.Y / TY) * (a.Z / TZ);
     const size_t smem = sizeof(__nv_bfloat16) * (27 * COUT * (CIN + 8) + HR * (TZ + 2) * (CIN + 8));
@@ -692,10 +450,9 @@ int evx_nn_conv_engine(void) { return g_engine.load(); }
 evx_status evx_nn_check(void) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return nn_cuda(e);
-    int flag = 0, zero = 0;
-    if ((e = cudaMemcpyFromSymbol(&flag, g_tc_timeout, sizeof(int))) != cudaSuccess) return nn_cuda(e);
+    int flag = 0;
+    if ((e = tc_take_timeout(&flag)) != cudaSuccess) return nn_cuda(e);
     if (!flag) return EVX_OK;
-    if ((e = cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int))) != cudaSuccess) return nn_cuda(e);
     return nn_fail(EVX_ERR_CUDA, "tensor-core convolution: a pipeline wait timed out (outputs invalid)");
 }
 

@@ -97,13 +97,16 @@ def _conv32(S, engine, shape, epi, seed):
     return out.float().cpu().numpy(), ref
 
 
-@pytest.mark.parametrize("shape", [(1, 3, 4, 64), (2, 2, 2, 128), (1, 5, 6, 192), (1, 1, 2, 64)])
+@pytest.mark.parametrize("shape", [(1, 3, 4, 64), (2, 2, 2, 128), (1, 5, 6, 192), (1, 1, 2, 64), (1, 3, 16, 128),
+                                   (1, 2, 50, 128), (2, 3, 4, 256)])
 @pytest.mark.parametrize("epi", [0, 1, 2, 3])
 def test_conv32_engines_agree_with_oracle(S, shape, epi):
     """32 -> 32 convolution on the tcgen05 engine and on the mma.sync engine:
     both within BF16 output rounding of the FP64 oracle, and within a few BF16
-    ulps of each other (same BF16 operands, FP32 accumulation in another order);
-    X = 1 and Y = 2 make every periodic neighbour wrap onto the tile itself."""
+    ulps of each other (same BF16 operands, FP32 accumulation in another order).
+    Z a multiple of 128 takes the pipelined kernel (Y = 16 and 50 split the
+    columns into y segments, 50 into ragged ones), other Z the tile kernel;
+    X = 1 and Y = 2 make periodic neighbours wrap onto the tile itself."""
     seed = sum(shape) * 10 + epi
     got_tc, ref = _conv32(S, S.ENGINE_TCGEN05, shape, epi, seed)
     got_ms, _ = _conv32(S, S.ENGINE_MMA_SYNC, shape, epi, seed)

@@ -1,36 +1,41 @@
 // tcgen05 engine of the surrogate's 32 -> 32 convolutions (sm_103a).
 //
 // Both kernels compute the periodic 3x3x3 convolution as an implicit GEMM on
-// the 5th-generation tensor cores: D[M voxels x 32 out channels] (FP32, in
-// tensor memory) += A[M x 16] (BF16 activations, shared memory) x B[16 x 32]
-// (BF16 weights, shared memory), 27 taps x 2 K-steps of 16 input channels.
-// Operands use the no-swizzle K-major core-matrix layout: a core matrix is
-// 8 rows x 16 bytes (8 channels) stored as 128 contiguous bytes; a
-// descriptor gives the byte distance between core matrices adjacent along K
-// (leading byte offset) and along M or N (stride byte offset). The weights
-// are [t][co/8][ci/8][8 co][8 ci]: LBO 128 B, SBO 512 B.
+// the 5th-generation tensor cores: D[128 voxels x N] (FP32, in tensor memory)
+// += A[128 x 16] (BF16 activations, shared memory) x B[16 x N] (BF16 weights,
+// shared memory), over the taps and 2 K-steps of 16 input channels. The
+// weights use the no-swizzle K-major core-matrix layout (a core matrix is
+// 8 rows x 16 bytes stored as 128 contiguous bytes; the descriptor gives the
+// distance of core matrices adjacent along K (leading byte offset, 128 B) and
+// along N (stride byte offset, 512 B)).
 //
 // conv_ring_kernel (Z a multiple of 128): a persistent, warp-specialised
 // pipeline. A work unit is a run of output rows (b, x, y = ys .. ye-1,
-// z0 .. z0+127); the 128 voxels of one row are the MMA's M. Per input row
-// (b, x-1 .. x+1, y') a ring slot holds the 3 x rows as [dx][ci/8][z][8 ci]
-// with z rows at a 16-byte pitch (row 8 + i holds z0 + i, rows 7 and 136
-// the periodic halo), so the z-shifted operand of tap dz starts dz rows
-// (dz * 16 bytes) later: LBO = one (dx, ci/8) run, SBO = 128 B.
-// Each output row needs 3 slots (y-1, y, y+1) and brings in one new slot.
-//   warp 0      producer: coalesced 16-byte cp.async of the slot's 3 x 130
-//               voxels (z0-1 .. z0+128, periodic), transposed into the runs
-//               on the way to shared memory; full/empty mbarriers per slot
-//   warp 1      one thread issues the 54 MMAs of a row, round-robin over
-//               KSPLIT partial accumulators so that consecutive MMAs do not
-//               wait on each other, into one of two row accumulators, and
-//               commits them to that accumulator's barrier and to the freed
-//               slot's barrier
-//   warps 2..9  epilogue: each warp sums the partials of 16 accumulator
-//               columns of its 32 lanes (tcgen05.ld), frees the accumulator,
-//               applies bias and the fused epilogue, stores BF16 channels-last
-// conv_tc_kernel (Z a multiple of 64): the same GEMM, unpipelined, per tile
-// of 2 rows x 64 z with three dz-shifted halo copies.
+// z0 .. z0+127); the 128 voxels of a row are the MMA's M. The kernel walks the
+// INPUT rows y' = ys-1 .. ye: a ring slot holds input row (b, x-1 .. x+1, y')
+// as [dx][z][32 ci] with 64-byte z rows in the 64-byte swizzle layout, exactly
+// as TMA writes it (row 16 + i holds z0 + i, rows 0..15 and 144..159 the
+// periodic halo), so the operand of tap dz starts dz rows later and its second
+// K-step 32 bytes on. One input row feeds output rows y'+1, y', y'-1 (dy = -1,
+// 0, +1): the weights of the three dy are stacked along N = 96, so each input
+// row costs 18 MMAs (3 dx x 3 dz x 2 K-steps) into three consecutive
+// accumulator blocks of a 16-block ring (32 columns per output row, descending
+// with the row so that the three blocks are adjacent; where they wrap past
+// column 511 each MMA splits into N = 64 + 32). Blocks start at zero and only
+// accumulate; an output row is complete after its third input row.
+//   warp 0      producer: per slot 9 TMA loads (per dx the 128 rows z0 ..
+//               and two 16-row halo boxes at (z0-16) mod Z, (z0+128) mod Z);
+//               full/empty mbarriers per slot
+//   warp 1      MMA issuer: the warp walks the schedule, lane 0 waits, issues
+//               and commits (slot freed after its 18 MMAs; a block's barrier
+//               once its output row is complete)
+//   warps 2..9  epilogue: each warp reads 16 columns of its 32 lanes of a
+//               completed block (tcgen05.ld), zeroes them (tcgen05.st), frees
+//               the block, applies bias and the fused epilogue and stores BF16
+//               channels-last; the two partial rows at each end of a unit are
+//               dropped
+// conv_tc_kernel (Z a multiple of 64): an unpipelined variant per tile of
+// 2 rows x 64 z with three dz-shifted no-swizzle halo copies, N = 32.
 //
 // Every mbarrier wait is bounded (about 1 s); a wait that runs out sets the
 // device flag g_tc_timeout, makes the other roles stop, waits (bounded) for
@@ -60,6 +65,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     d |= (uint64_t)1 << 46;  // descriptor version (sm_100 family); no swizzle, base offset 0
     return d;
 }
+
+// K-major operand in the 64-byte swizzle layout (rows of 64 bytes, 16-byte
+// chunks permuted by address bits 7..8 within 512-byte atoms): rows 64 bytes
+// apart, 8-row groups 512 bytes apart. The permutation follows the absolute
+// shared-memory address (as TMA applies it), so a start moved by whole rows
+// or by 32 bytes addresses the same stored layout.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) { return sdesc(saddr, 16, 512) | (4ull << 61); }
 
 // instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N, M
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -192,16 +204,17 @@ __device__ __forceinline__ void stage_weights(unsigned char* swb, const __nv_bfl
 // ----------------------------------------------- pipelined scatter kernel
 namespace ring {
 constexpr int ZT = 128;                    // voxels per output row tile (MMA M)
-constexpr int RP = 144;                    // z rows per (dx, ci/8) run: z0 + i at row 8 + i, halo rows 0..7, 136..143
-constexpr int NS = 4;                      // ring slots (one input row each)
-constexpr int SLOT = 3 * 4 * RP * 16;      // bytes per slot
+constexpr int RZ = 160;                    // z rows (64 bytes each) per x-row run: z0 + i at row 16 + i
+constexpr int RUN = RZ * 64;               // bytes per run (a multiple of 1024)
+constexpr int NS = 5;                      // ring slots (one input row each)
+constexpr int SLOT = 3 * RUN;              // bytes per slot: runs for x-1, x, x+1
 constexpr int WB = 9 * 12 * 4 * 128;       // staged weights: [dx][dz][n/8 (12)][ci/8][8 n][8 ci]
 constexpr int NBLK = 16;                   // accumulator blocks of 32 columns (a ring over output rows)
 constexpr int NEPI = 8;                    // epilogue warps
 constexpr int NTH = (2 + NEPI) * 32;
 constexpr int BAR = WB + NS * SLOT;        // barriers: full[NS], empty[NS], tfull[NBLK], tempty[NBLK]
-constexpr int SMEM = BAR + 8 * (2 * NS + 2 * NBLK) + 16 + 128;  // + tensor-memory slot, abort flag, alignment
-constexpr uint32_t SLOT_TX = 12 * RP * 16; // TMA bytes per slot: 12 runs of 128 + 2 x 8 z rows
+constexpr int SMEM = BAR + 8 * (2 * NS + 2 * NBLK) + 16 + 1024;  // + tensor-memory slot, abort flag, alignment
+constexpr uint32_t SLOT_TX = SLOT;         // TMA bytes per slot
 constexpr long long WAIT_BUDGET = 1LL << 31;
 }  // namespace ring
 
@@ -240,10 +253,11 @@ __device__ __forceinline__ void ring_unit(const RingArgs& r, int u, int& bx, int
 __device__ __forceinline__ uint32_t ring_blk(uint32_t v) { return (ring::NBLK - v % ring::NBLK) % ring::NBLK; }
 
 // MMA q = 2 (3 dxi + dzi) + ks of an input row: descriptor offsets (16-byte
-// units) of its A operand (from the slot's run (dx = -1, ci/8 = 0), z row 7)
-// and of its B operand (from the staged weights)
+// units) of its A operand (from the slot's first run: z row 15 + dzi of run
+// dxi, plus 32 bytes for the second K-step) and of its B operand (from the
+// staged weights)
 __host__ __device__ constexpr uint64_t ring_aoff(int q) {
-    return (uint64_t)((((q >> 1) / 3) * 4 + 2 * (q & 1)) * ring::RP + (q >> 1) % 3);
+    return (uint64_t)(((q >> 1) / 3) * (ring::RUN / 16) + (15 + (q >> 1) % 3) * 4 + 2 * (q & 1));
 }
 __host__ __device__ constexpr uint64_t ring_boff(int q) { return (uint64_t)(((q >> 1) * 12 * 4 + 2 * (q & 1)) * 8); }
 
@@ -260,7 +274,7 @@ __global__ void __launch_bounds__(ring::NTH, 1)
     conv_ring_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap hmap, RingArgs r) {
     using namespace ring;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char* sm = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);  // 128-byte aligned base
+    unsigned char* sm = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);  // swizzle atoms: 1024-aligned
     unsigned char* swb = sm;
     unsigned char* sring = sm + WB;
     const uint32_t full = smem_addr(sm + BAR), empty = full + 8 * NS, tfull = empty + 8 * NS,
@@ -330,17 +344,15 @@ __global__ void __launch_bounds__(ring::NTH, 1)
                 }
                 if (lane == 0) {
                     const uint32_t base = smem_addr(sring + slot * SLOT);
-                    const int zl = (z0 - 8 + Z) % Z, zr = (z0 + ZT) % Z;  // periodic z halo: 8-row boxes
+                    const int zl = (z0 - 16 + Z) % Z, zr = (z0 + ZT) % Z;  // periodic z halo: 16-row boxes
                     mbar_expect_tx(full + 8 * slot, SLOT_TX);
+#pragma unroll
                     for (int dxi = 0; dxi < 3; ++dxi) {
                         const int bxx = b * X + (x + dxi - 1 + X) % X;
-#pragma unroll
-                        for (int cig = 0; cig < 4; ++cig) {
-                            const uint32_t run = base + (dxi * 4 + cig) * RP * 16;
-                            tma_load4(run + 8 * 16, &map, cig * 8, z0, yp, bxx, full + 8 * slot);
-                            tma_load4(run, &hmap, cig * 8, zl, yp, bxx, full + 8 * slot);
-                            tma_load4(run + (8 + ZT) * 16, &hmap, cig * 8, zr, yp, bxx, full + 8 * slot);
-                        }
+                        const uint32_t run = base + dxi * RUN;
+                        tma_load4(run + 16 * 64, &map, 0, z0, yp, bxx, full + 8 * slot);
+                        tma_load4(run, &hmap, 0, zl, yp, bxx, full + 8 * slot);
+                        tma_load4(run + (16 + ZT) * 64, &hmap, 0, zr, yp, bxx, full + 8 * slot);
                     }
                 }
                 __syncwarp();
@@ -360,24 +372,32 @@ __global__ void __launch_bounds__(ring::NTH, 1)
         const uint32_t ring0 = smem_addr(sring);
         const uint64_t bdesc0 = sdesc(smem_addr(swb), 128, 512);
         uint32_t k = 0, V = 0, last_v = 0;
+        uint32_t vready = NBLK - 1;  // virtual rows <= vready have a free (zeroed) accumulator block
         bool ok = true, issued = false;
         for (int u = blockIdx.x; u < r.nunits && ok; u += gridDim.x) {
             int bx, z0, ys, ye;
             ring_unit(r, u, bx, z0, ys, ye);
             const uint32_t L = (uint32_t)(ye - ys);
             for (uint32_t i = 0; i <= L + 1; ++i, ++k) {
+                // blocks are claimed 8 rows at a time (rows up to V+i+9, freed by the epilogue
+                // once it has read rows up to V+i-7), so the tensor-memory fence that orders
+                // the epilogue's reads before these MMAs runs once per 8 input rows
+                const bool claim = V + i + 2 > vready;
                 uint32_t w_ok = 1;
                 if (lane == 0) {
-                    w_ok = ring_wait(full + 8 * (k % NS), (k / NS) & 1, abort_flag);
-                    for (uint32_t v = (i == 0 ? V : V + i + 2); v <= V + i + 2 && w_ok; ++v)
-                        if (v >= NBLK) w_ok = ring_wait(tempty + 8 * ring_blk(v), ((v / NBLK) & 1) ^ 1, abort_flag);
+                    for (uint32_t v = vready + 1; claim && v <= V + i + 9 && w_ok; ++v)
+                        w_ok = ring_wait(tempty + 8 * ring_blk(v), ((v / NBLK) & 1) ^ 1, abort_flag);
+                    if (w_ok) w_ok = ring_wait(full + 8 * (k % NS), (k / NS) & 1, abort_flag);
                 }
                 if (!__shfl_sync(0xffffffffu, w_ok, 0)) {
                     ok = false;
                     break;
                 }
-                fence_after();
-                const uint64_t adesc = sdesc(ring0 + (k % NS) * SLOT + 7 * 16, RP * 16, 128);
+                if (claim) {
+                    vready = V + i + 9;
+                    fence_after();
+                }
+                const uint64_t adesc = sdesc_sw64(ring0 + (k % NS) * SLOT);
                 const uint32_t b0 = ring_blk(V + i + 2);  // blocks b0, b0+1, b0+2 (mod 16)
                 // 18 MMAs (dx, dz, ks); where the three blocks wrap past the last
                 // column, each splits into two. One branch per input row keeps the
@@ -606,16 +626,17 @@ PFN_cuTensorMapEncodeTiled_v12000 nn_encode_fn() {
     return fn;
 }
 
-// activations [B X][Y][Z][32] as a 4D BF16 tensor (32 channels, Z, Y, B X), box 8 channels x zrows z
+// activations [B X][Y][Z][32] as a 4D BF16 tensor (32 channels, Z, Y, B X), box 32 channels x zrows z,
+// written to shared memory in the 64-byte swizzle layout
 bool ring_map(CUtensorMap* m, const ConvArgs& a, int zrows) {
     auto fn = nn_encode_fn();
     if (!fn || ((uintptr_t)a.in & 15)) return false;
     const cuuint64_t dims[4] = {32, (cuuint64_t)a.Z, (cuuint64_t)a.Y, (cuuint64_t)a.B * a.X};
     const cuuint64_t strides[3] = {64, (cuuint64_t)a.Z * 64, (cuuint64_t)a.Y * a.Z * 64};
-    const cuuint32_t box[4] = {8, (cuuint32_t)zrows, 1, 1};
+    const cuuint32_t box[4] = {32, (cuuint32_t)zrows, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(a.in), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -623,7 +644,7 @@ template <int EPI>
 cudaError_t launch_ring(const ConvArgs& a, cudaStream_t st, int sms, bool* launched) {
     *launched = false;
     CUtensorMap map, hmap;
-    if (a.Z % ring::ZT || !ring_map(&map, a, ring::ZT) || !ring_map(&hmap, a, 8)) return cudaSuccess;
+    if (a.Z % ring::ZT || !ring_map(&map, a, ring::ZT) || !ring_map(&hmap, a, 16)) return cudaSuccess;
     RingArgs r{};
     r.a = a;
     r.nzc = a.Z / ring::ZT;

@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--train-iters", type=int, default=200)
+    ap.add_argument("--conv-probe", default=None, metavar="B,X,Y,Z",
+                    help="only time the surrogate's 32->32 convolution (plain epilogue) on this shape and exit")
     return ap.parse_args()
 
 
@@ -232,25 +234,38 @@ def surrogate_bench(args):
                         "block_evaluations": st["blocks"], "fallbacks": st["fallbacks"],
                         "t_net_s": st["t_net_s"], "t_guard_s": st["t_guard_s"],
                         "t_fallback_s": st["t_fallback_s"]}
-    # conv 32 -> 32 throughput at 256^3 x 8 (dominant surrogate kernel)
+    # conv 32 -> 32 throughput at 256^3 x 8 (dominant surrogate kernel), both engines
     X, Y, Z = shape
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(2):
-        inf._conv(inf.h[0], "W1_0", inf.p["b1_0"], inf.a[0], 32, 32, S.EPI_GELU, pre=inf.u[0])
-    e0.record()
-    reps = 5
-    for _ in range(reps):
-        inf._conv(inf.h[0], "W1_0", inf.p["b1_0"], inf.a[0], 32, 32, S.EPI_GELU, pre=inf.u[0])
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
     flops = 2.0 * 27 * 32 * 32 * NB * X * Y * Z
     peak, src = bf16_peak()
-    out["conv_roofline"] = {"bound": "tensor", "kernel": "conv_fwd_kernel<32,32,GELU> (mma.sync bf16)",
+
+    def conv_ms(engine):
+        S.set_conv_engine(engine)
+        try:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            for _ in range(2):
+                inf._conv(inf.h[0], "W1_0", inf.p["b1_0"], inf.a[0], 32, 32, S.EPI_GELU, pre=inf.u[0])
+            e0.record()
+            reps = 5
+            for _ in range(reps):
+                inf._conv(inf.h[0], "W1_0", inf.p["b1_0"], inf.a[0], 32, 32, S.EPI_GELU, pre=inf.u[0])
+            e1.record()
+            S.check()
+            return e0.elapsed_time(e1) / reps
+        finally:
+            S.set_conv_engine(S.ENGINE_TCGEN05)
+
+    ms = conv_ms(S.ENGINE_TCGEN05)
+    ms_sync = conv_ms(S.ENGINE_MMA_SYNC)
+    out["conv_roofline"] = {"bound": "tensor",
+                            "kernel": "conv_ring_kernel<GELU> (tcgen05.mma bf16, TMEM accumulators, TMA ring)",
                             "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                             "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_source": src + " bf16_tflops",
-                            "ms_per_launch": ms}
+                            "ms_per_launch": ms,
+                            "mma_sync_engine": {"kernel": "conv_fwd_kernel<32,32,GELU> (mma.sync bf16)",
+                                                "ms_per_launch": ms_sync,
+                                                "achieved": flops / (ms_sync * 1e-3) / 1e12}}
     del inf
     torch.cuda.empty_cache()
     return out
@@ -285,10 +300,43 @@ def run_reference(args):
     }), flush=True)
 
 
+def conv_probe(spec):
+    """Times the surrogate's 32 -> 32 convolution (default engine, plain
+    epilogue) on one shape: a small, self-contained case for profilers."""
+    import torch
+    from paper_2507_21748_gb300 import surrogate as S
+    B, X, Y, Z = (int(v) for v in spec.split(","))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((B, X, Y, Z, 32), device="cuda", generator=g).to(torch.bfloat16)
+    w = (torch.randn((27, 32, 32), device="cuda", generator=g) * 0.1).to(torch.bfloat16)
+    b = torch.randn(32, device="cuda", generator=g)
+    out = torch.empty_like(x)
+
+    def run():
+        S._ck(S.lib.evx_nn_conv3d(S._p(x), S._p(w), S._p(b), S._p(out), None, None, B, X, Y, Z, 32, 32,
+                                  S.EPI_PLAIN, S._stream()))
+
+    for _ in range(3):
+        run()
+    S.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        run()
+    e1.record()
+    S.check()
+    ms = e0.elapsed_time(e1) / 5
+    flops = 2.0 * 27 * 32 * 32 * B * X * Y * Z
+    print(json.dumps({"conv_probe": [B, X, Y, Z], "engine": S.conv_engine(), "ms": ms,
+                      "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.conv_probe:
+        return conv_probe(args.conv_probe)
     import torch
     ws, rank, local = dist_env()
     if ws > 1:

@@ -101,10 +101,34 @@ evx_status evx_get_field(evx_grid *g, float *d_out);
 /* Same into host memory; synchronises the stream. */
 evx_status evx_get_field_host(evx_grid *g, float *h_out);
 
-/* Advance the state by n_steps >= 0 semi-implicit steps (update above).
- * Asynchronous: the steps are issued on the grid's stream (as CUDA-graph
- * launches when profiling is off). */
+/* Advance the state by n_steps >= 0 semi-implicit Cahn-Hilliard steps
+ * (update above). Asynchronous: the steps are issued on the grid's stream (as
+ * CUDA-graph launches when profiling is off). EVX_ERR_STATE if the grid is set
+ * to another model. */
 evx_status evx_ch_step(evx_grid *g, int n_steps);
+
+/* Models the step engine runs (default EVX_MODEL_CH).
+ *
+ * EVX_MODEL_AC: the Allen-Cahn equation for a non-conserved order parameter
+ * (paper: Eq. (allen-cahn) of subsection "Phase transformations of first and
+ * second order"), under the same readings as above (gamma0 = 1, kappa =
+ * 2 gamma0 eps, f'(c) = c^3 - c) with the kinetic coefficient L = p.M:
+ *   c_t = -L (c^3 - c - kappa lap c).
+ * Subsection "Semi-implicit timestepping" with S = -L kappa |k|^2 gives
+ *   c_hat' = (c_hat - dt L F{c^3 - c}) / (1 + dt L kappa |k|^2).
+ * The k = 0 mode is not conserved: the FP64 mean moves by
+ *   cbar' = cbar - dt L mean(c^3 - c)
+ * with the mean of the nonlinearity summed in FP64 from per-CTA partials.
+ * Same four passes (plus a one-block mean update), same sizes, energy and
+ * field calls; evx_ch_adjoint and evx_ch_step_static are Cahn-Hilliard only.
+ * Changing the model drops the captured step graphs (synchronises). */
+typedef enum { EVX_MODEL_CH = 0, EVX_MODEL_AC = 1 } evx_model;
+evx_status evx_set_model(evx_grid *g, int model);
+int evx_get_model(const evx_grid *g); /* -1 for NULL */
+
+/* Advance the state by n_steps >= 0 steps of the grid's model (either one);
+ * asynchronous, as evx_ch_step. */
+evx_status evx_step(evx_grid *g, int n_steps);
 
 /* Ginzburg-Landau energy and mass of the current field, in FP64 (paper:
  * F_int of subsection "Phase transformations", in the c in [-1, 1] form):
@@ -137,7 +161,7 @@ evx_status evx_ch_adjoint(evx_grid *g, const float *d_c0, int n_steps, int ckpt_
 /* Device memory the grid holds, in bytes (buffers + tables + scratch). */
 evx_status evx_footprint(const evx_grid *g, size_t *bytes);
 
-/* Per-pass timing. With profiling on, evx_ch_step issues its kernels
+/* Per-pass timing. With profiling on, evx_step / evx_ch_step issue their kernels
  * without CUDA graphs and records a CUDA event pair around every pass on the
  * grid's stream; evx_pass_times (synchronises) returns, for each of the four
  * step passes (0: x pass + update, 1: y inverse, 2: z C2R + c^3-c + R2C,

@@ -280,6 +280,8 @@ extern "C" evx_status evx_ch_adjoint(evx_grid* g, const float* d_c0, int n_steps
                                      const float* d_dLdcN, float* d_dLdc0, double* dLdkappa,
                                      double* dLdM) {
     if (!g || !d_c0 || !d_dLdcN || !d_dLdc0) return set_error(g, EVX_ERR_ARG, "NULL argument");
+    if (g->model != EVX_MODEL_CH)
+        return set_error(g, EVX_ERR_STATE, "the adjoint is implemented for the Cahn-Hilliard model only");
     if (n_steps < 0 || ckpt_every < 1) return set_error(g, EVX_ERR_ARG, "bad n_steps / ckpt_every");
     if ((((uintptr_t)d_c0) | ((uintptr_t)d_dLdcN) | ((uintptr_t)d_dLdc0)) & 7u)
         return set_error(g, EVX_ERR_ARG, "field pointers must be 8-byte aligned");

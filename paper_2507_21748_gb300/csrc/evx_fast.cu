@@ -121,8 +121,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // ------------------------------------------------ z pass: C2R, c^3 - c, R2C
-template <int TP, int NTZ>
+template <int TP, int NTZ, bool GS>
 __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int ntiles) {
+    // GS (Allen-Cahn): also sum g(c) - g(cbar) over the grid, FP32 per thread and
+    // tile, FP64 across tiles, one FP64 partial per CTA in a.gsum[blockIdx.x]
     constexpr int M = 32 * TP, NB = 32 / TP, RPC = NTZ / TP, RS = M + TP;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp, Zh = a.Zp / 2;
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
     const float c3 = (float)(3.0 * cbd);
     const float s = a.scale;
     auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB; };
+    double gacc = 0.0;
     for (; tile < ntiles; tile += gridDim.x) {
         const long long row0 = (long long)tile * RPC;
         cp_wait<0>();
@@ -192,6 +195,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
         // real-space samples z[m] = c[2m] + i c[2m+1], m = k1 + 32 k2
         const long long row = row0 + r;
         const bool rowok = row < a.nrows;
+        float gtile = 0.f;  // rows past the end were loaded as zeros: d = 0 adds nothing
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
@@ -204,7 +208,9 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
                 // g(c) - g(cbar) = d (g'(cbar) + d (3 cbar + d)); the constant g(cbar) only
                 // feeds the k = 0 mode, which the update multiplies by b(0) = 0
                 v[i * TP + c] = make_float2(d0 * fmaf(d0, c3 + d0, gp), d1 * fmaf(d1, c3 + d1, gp));
+                if (GS) gtile += v[i * TP + c].x + v[i * TP + c].y;
             }
+        if (GS) gacc += (double)gtile;
         // forward complex FFT of length M from block ownership (m = a + 32 b)
         pass_b<TP, -1>(v);
         twiddle_b<TP, -1>(v, n2, tB);
@@ -239,6 +245,18 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
             if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
         }
         if (rowok && n2 == 0) out[M] = make_float2(v[0].x - v[0].y, 0.f);  // X_M = Re Z_0 - Im Z_0
+    }
+    if (GS) {  // fixed-order CTA reduction of the FP64 sums
+        __shared__ double red[NTZ / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gacc += __shfl_down_sync(0xffffffffu, gacc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gacc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NTZ / 32; ++w) t += red[w];
+            a.gsum[blockIdx.x] = t;
+        }
     }
 }
 
@@ -366,7 +384,7 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
 }
 
 // x pass + update with TMA: boxes {8, 1, BOX (x), 1}
-template <int TP>
+template <int TP, bool AC>
 __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int ntiles,
                                                               const __grid_constant__ CUtensorMap mW,
                                                               const __grid_constant__ CUtensorMap mS,
@@ -409,7 +427,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
     for (; tile < ntiles; tile += gridDim.x) {
         const int ky = tile / nchunks, chunk = tile - ky * nchunks;
         const int next = tile + gridDim.x;
-        // ---- g_hat = F_x W, kept as G = -dt M |k|^2 g_hat
+        // ---- g_hat = F_x W, kept as G = -dt M |k|^2 g_hat (Allen-Cahn: -dt L g_hat)
         bool ok = mbar_wait(bars + 0, parity);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
@@ -433,7 +451,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) {
-                const float f = ndtM * (k2xs[n2 * NB + i + 32 * c] + k2yz);
+                const float f = AC ? ndtM : ndtM * (k2xs[n2 * NB + i + 32 * c] + k2yz);
                 G[i * TP + c] = cscale(v[i * TP + c], f);
             }
         // ---- c_hat = F_x S
@@ -452,12 +470,13 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         t1_s<TP, 8>(v, xb, n2, p);
         pass_b<TP, -1>(v);
         // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L; k = 0 stays out
+        //      (Allen-Cahn: (c_hat - dt L g_hat) / (1 + dt L kappa |k|^2) / L)
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) {
                 const float k2 = k2xs[n2 * NB + i + 32 * c] + k2yz;
-                const float f = a.invL * rcp_approx(fmaf(a.dtMk, k2 * k2, 1.f));
+                const float f = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
                 v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), f);
             }
         if (ky == 0 && kz == 0 && n2 == 0) v[0] = make_float2(0.f, 0.f);
@@ -617,14 +636,15 @@ static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) 
         return false;
     const size_t smem = sizeof(float2) * (2 * L * 8 + (L + TP) * 8 + 2 * L) + sizeof(float) * L + 16;
     int per = 0;
-    cudaError_t e = prep(fast::fxupd_tma_kernel<TP>, smem, 8 * TP, &per);
+    auto kern = a.model == 1 ? fast::fxupd_tma_kernel<TP, true> : fast::fxupd_tma_kernel<TP, false>;
+    cudaError_t e = prep(kern, smem, 8 * TP, &per);
     if (e != cudaSuccess) {
         *err = e;
         return true;
     }
     const int ntiles = a.nchunks * a.ny;
     const int grid = std::min(ntiles, per * num_sms());
-    fast::fxupd_tma_kernel<TP><<<grid, 8 * TP, smem, st>>>(a, ntiles, mw, ms, mo);
+    kern<<<grid, 8 * TP, smem, st>>>(a, ntiles, mw, ms, mo);
     *err = cudaGetLastError();
     return true;
 }
@@ -656,27 +676,29 @@ bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
 }
 
 template <int TP>
-static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st) {
+static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st, int* grid_used) {
     constexpr int NTZ = 128, RPC = NTZ / TP, RS = 32 * TP + TP;
     const int BS = TP + (((a.Zp > RS ? a.Zp : RS) - TP + 15) & ~15);  // as in the kernel
     const size_t smem = sizeof(float2) * ((size_t)RPC * BS + 3 * 32 * TP + 1);
     int per = 0;
-    cudaError_t e = prep(fast::fzstep_kernel<TP, NTZ>, smem, NTZ, &per);
+    auto kern = a.gsum ? fast::fzstep_kernel<TP, NTZ, true> : fast::fzstep_kernel<TP, NTZ, false>;
+    cudaError_t e = prep(kern, smem, NTZ, &per);
     if (e != cudaSuccess) return e;
     const int ntiles = (int)((a.nrows + RPC - 1) / RPC);
     const int grid = std::min(ntiles, per * num_sms());
-    fast::fzstep_kernel<TP, NTZ><<<grid, NTZ, smem, st>>>(a, ntiles);
+    if (grid_used) *grid_used = grid;
+    kern<<<grid, NTZ, smem, st>>>(a, ntiles);
     return cudaGetLastError();
 }
 
-bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err) {
+bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used) {
     const int TP = tp_of(a.M);
     if (TP < 2 || TP > 16) return false;
     switch (TP) {
-        case 2: *err = run_fzstep<2>(a, st); return true;
-        case 4: *err = run_fzstep<4>(a, st); return true;
-        case 8: *err = run_fzstep<8>(a, st); return true;
-        case 16: *err = run_fzstep<16>(a, st); return true;
+        case 2: *err = run_fzstep<2>(a, st, grid_used); return true;
+        case 4: *err = run_fzstep<4>(a, st, grid_used); return true;
+        case 8: *err = run_fzstep<8>(a, st, grid_used); return true;
+        case 16: *err = run_fzstep<16>(a, st, grid_used); return true;
     }
     return false;
 }

@@ -14,6 +14,7 @@ struct evx_grid {
     int nx = 0, ny = 0, nz = 0, M = 0, Zp = 0, PZ = 0, zrows = 0;
     int YB = 0;                  // y block of the spectral layout (choose_yblock)
     evx_params p{};
+    int model = EVX_MODEL_CH;    // evx_set_model
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
     float2* S = nullptr;

@@ -54,6 +54,8 @@ struct XUpdArgs {
     const float* k2y;   // (ny)
     const float* k2z;   // (M + 1)
     float dtM, dtMk, invL;
+    int model;          // 0 Cahn-Hilliard: b = -dt M |k|^2, D = 1 + dt M kappa |k|^4
+                        // 1 Allen-Cahn:    b = -dt L,       D = 1 + dt L kappa |k|^2
 };
 
 // Energy: gradient term sum_k w(kz) |k|^2 |c_hat|^2 from the state S.
@@ -92,6 +94,7 @@ struct ZPassArgs {
     float scale;            // 1 / (ny nz)
     const double* cbar;     // FP64 mean (Z_STEP, Z_C2R); may be null (0)
     double* partials;       // bulk energy partial per CTA (Z_C2R) or null
+    double* gsum;           // Z_STEP, Allen-Cahn: per-CTA FP64 sums of g(c) - g(cbar), or null
     // map_rows = 1: real rows rin / rout are a caller's C-order field; memory
     // row r of the y-blocked spectrum is caller row x * ny + y
     int map_rows, YB, nxr, nyr;
@@ -105,7 +108,9 @@ __host__ __device__ inline long long user_row(long long r, int YB, int nx, int n
 cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st);
 cudaError_t launch_xupdate(const XUpdArgs& a, cudaStream_t st);
 cudaError_t launch_xenergy(const XEnergyArgs& a, cudaStream_t st);
-cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st, int* grid_used = nullptr);
+// Allen-Cahn mean: cbar <- cbar - dtL (g(cbar) + sum(gsum[0..n)) / V), one block, fixed order
+cudaError_t launch_ac_mean(const double* gsum, int n, double* cbar, double dtL, double invV, cudaStream_t st);
 int zpass_grid(const ZPassArgs& a);
 int xenergy_grid(const XEnergyArgs& a);
 // deterministic FP64 sums
@@ -122,7 +127,7 @@ constexpr int SUM_BLOCKS = 1216;  // 8 x 152 SMs
 // fast paths for power-of-two lengths (evx_fast.cu); return false if not applicable
 bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err);
 bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err);
-bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err);
+bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used);
 bool fast_paths_enabled();  // false when the environment sets EVX_GENERIC=1
 // reads (and optionally clears) the flag a bounded TMA wait sets when it gives up
 bool fast_timeout_flag(int* flag, bool clear);

@@ -124,8 +124,10 @@ __global__ void __launch_bounds__(NT, 1) xupdate_kernel(XUpdArgs a) {
         const int kz = col0 + p;
         if (kz < a.ncols) {
             const float k2 = a.k2x[i] + k2y + a.k2z[kz];
-            const float ainv = a.invL / fmaf(a.dtMk, k2 * k2, 1.f);
-            const float b = -a.dtM * k2 * ainv;
+            // Cahn-Hilliard: a = 1/D, b = -dt M |k|^2 / D, D = 1 + dt M kappa |k|^4;
+            // Allen-Cahn:   a = 1/D, b = -dt L / D,       D = 1 + dt L kappa |k|^2
+            const float ainv = a.invL / fmaf(a.dtMk, a.model == 1 ? k2 : k2 * k2, 1.f);
+            const float b = -a.dtM * (a.model == 1 ? 1.f : k2) * ainv;
             const float2 c = tile[i * (2 * SP) + SP + p];
             float2 r = make_float2(ainv * c.x, ainv * c.y);
             if (haveW) {
@@ -270,7 +272,9 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
                         reinterpret_cast<float2*>(a.rout + (row0 + r) * a.rpitch)[n] = make_float2(c0, c1);
                     // g(c) - g(cbar) from d = c - cbar (see the fast z pass)
                     const float d0 = z.x * s, d1 = z.y * s;
-                    tile[r * PZ + n] = make_float2(d0 * fmaf(d0, c3 + d0, gp), d1 * fmaf(d1, c3 + d1, gp));
+                    const float2 gv = make_float2(d0 * fmaf(d0, c3 + d0, gp), d1 * fmaf(d1, c3 + d1, gp));
+                    tile[r * PZ + n] = gv;
+                    if (a.gsum) acc += (double)gv.x + (double)gv.y;
                 } else {  // Z_C2R
                     const long long rr = a.map_rows ? user_row(row0 + r, a.YB, a.nxr, a.nyr) : row0 + r;
                     if (a.rout)
@@ -288,6 +292,10 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
                 if (threadIdx.x == 0) a.partials[blockIdx.x] = acc;
             }
             return;
+        }
+        if (MODE == Z_STEP && a.gsum) {  // uniform: every thread of the CTA takes it
+            acc = block_sum_double(acc, ws);
+            if (threadIdx.x == 0) a.gsum[blockIdx.x] = acc;
         }
         __syncthreads();
     }
@@ -341,6 +349,20 @@ __global__ void __launch_bounds__(1024) reduce_partials_kernel(const double* par
     for (int i = threadIdx.x; i < n; i += 1024) acc += partials[i];
     acc = block_sum_double(acc, ws);
     if (threadIdx.x == 0) *out = acc * scale;
+}
+
+// Allen-Cahn: the k = 0 mode of the update has D = 1, so the FP64 mean moves by
+// cbar' = cbar - dt L mean(g(c)), mean(g(c)) = g(cbar) + sum(g(c) - g(cbar)) / V
+__global__ void __launch_bounds__(1024) ac_mean_kernel(const double* gsum, int n, double* cbar, double dtL,
+                                                        double invV) {
+    __shared__ double ws[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) acc += gsum[i];
+    acc = block_sum_double(acc, ws);
+    if (threadIdx.x == 0) {
+        const double c = *cbar;
+        *cbar = c - dtL * (c * c * c - c + acc * invV);
+    }
 }
 
 __global__ void cadd_kernel(const float2* a, const float2* b, float2* out, long long n) {
@@ -411,11 +433,12 @@ int zpass_grid(const ZPassArgs& a) {
     return (int)((a.nrows + a.rows_per_cta - 1) / a.rows_per_cta);
 }
 
-cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st) {
+cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st, int* grid_used) {
     cudaError_t fe;
-    if (mode == Z_STEP && fast_paths_enabled() && fast_zstep(a, st, &fe)) return fe;
+    if (mode == Z_STEP && fast_paths_enabled() && fast_zstep(a, st, &fe, grid_used)) return fe;
     const size_t sm = zpass_smem(a.M, a.PZ, a.rows_per_cta);
     const int grid = zpass_grid(a);
+    if (grid_used) *grid_used = grid;
     cudaError_t e = cudaSuccess;
     switch (mode) {
         case Z_STEP:
@@ -443,6 +466,11 @@ cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st) {
 cudaError_t launch_sum_field(const float* c, long long nrows, int rowlen, long long pitch,
                              double* partials, int nblocks, cudaStream_t st) {
     sum_rows_kernel<<<nblocks, NT, 0, st>>>(c, nrows, rowlen, pitch, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ac_mean(const double* gsum, int n, double* cbar, double dtL, double invV, cudaStream_t st) {
+    ac_mean_kernel<<<1, 1024, 0, st>>>(gsum, n, cbar, dtL, invV);
     return cudaGetLastError();
 }
 

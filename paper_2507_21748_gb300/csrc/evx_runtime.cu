@@ -153,6 +153,7 @@ XUpdArgs x_args(const evx_grid* g, const float2* W, float2* S, float2* S_out, do
     a.dtM = (float)(dt * M);
     a.dtMk = (float)(dt * M * kappa);
     a.invL = (float)(1.0 / g->nx);
+    a.model = g->model == EVX_MODEL_AC ? 1 : 0;
     return a;
 }
 
@@ -189,7 +190,16 @@ static cudaError_t issue_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) {
     z.in = g->W;
     z.out = g->W;
     z.cbar = g->d_scal;
-    if ((e = launch_zpass(z, Z_STEP, st)) != cudaSuccess) return e;
+    const bool ac = g->model == EVX_MODEL_AC;
+    if (ac) z.gsum = g->d_part;  // Allen-Cahn: the mean moves by -dt L mean(g(c))
+    int zgrid = 0;
+    if ((e = launch_zpass(z, Z_STEP, st, &zgrid)) != cudaSuccess) return e;
+    if (ac) {
+        const double V = (double)g->nx * g->ny * g->nz;
+        if (zgrid <= 0 || zgrid > g->npart) return cudaErrorInvalidValue;
+        if ((e = launch_ac_mean(g->d_part, zgrid, g->d_scal, g->p.dt * g->p.M, 1.0 / V, st)) != cudaSuccess)
+            return e;
+    }
     if (ev) cudaEventRecord(ev[2], st);
     if ((e = launch_spass(y_args(g, g->W, g->W), -1, st)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[3], st);
@@ -453,7 +463,26 @@ evx_status evx_get_field_host(evx_grid* g, float* h_out) {
     return check_timeouts(g);
 }
 
+evx_status evx_set_model(evx_grid* g, int model) {
+    if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
+    if (model != EVX_MODEL_CH && model != EVX_MODEL_AC) return fail(g, EVX_ERR_ARG, "unknown model %d", model);
+    if (model != g->model) {
+        CK(cudaStreamSynchronize(g->st));
+        drop_graphs(g);
+        g->model = model;
+    }
+    return EVX_OK;
+}
+
+int evx_get_model(const evx_grid* g) { return g ? g->model : -1; }
+
 evx_status evx_ch_step(evx_grid* g, int n_steps) {
+    if (g && g->model != EVX_MODEL_CH)
+        return fail(g, EVX_ERR_STATE, "evx_ch_step on a grid set to another model (use evx_step)");
+    return evx_step(g, n_steps);
+}
+
+evx_status evx_step(evx_grid* g, int n_steps) {
     if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
     if (n_steps < 0) return fail(g, EVX_ERR_ARG, "n_steps < 0");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");

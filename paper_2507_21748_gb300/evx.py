@@ -22,8 +22,9 @@ EXPORTS = [
     "evx_grid_create", "evx_grid_destroy", "evx_set_params", "evx_set_stream", "evx_set_field",
     "evx_set_field_host", "evx_get_field", "evx_get_field_host", "evx_ch_step", "evx_energy",
     "evx_mean", "evx_ch_adjoint", "evx_footprint", "evx_set_profiling", "evx_pass_times",
-    "evx_pass_bytes", "evx_ch_step_static", "evx_last_error",
+    "evx_pass_bytes", "evx_ch_step_static", "evx_set_model", "evx_get_model", "evx_step", "evx_last_error",
 ]
+MODELS = {"ch": 0, "ac": 1}  # evx_model: Cahn-Hilliard, Allen-Cahn
 
 
 class EvxError(RuntimeError):
@@ -62,6 +63,9 @@ def _load():
         "evx_pass_times": ([vp, dp, ctypes.POINTER(ctypes.c_longlong), i], st),
         "evx_pass_bytes": ([vp, i, dp], st),
         "evx_ch_step_static": ([fp, fp, i, i, i, Params, i, vp], st),
+        "evx_set_model": ([vp, i], st),
+        "evx_get_model": ([vp], ctypes.c_int),
+        "evx_step": ([vp, i], st),
         "evx_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -88,9 +92,11 @@ def _check_field(t, shape):
 
 
 class Grid:
-    """A periodic nx*ny*nz Cahn-Hilliard grid owned by libevx."""
+    """A periodic nx*ny*nz grid owned by libevx, stepping the Cahn-Hilliard model
+    (``model="ch"``, default) or the Allen-Cahn model (``model="ac"``, M is then
+    the kinetic coefficient L)."""
 
-    def __init__(self, shape, dt=0.1, M=1.0, kappa=1.0, h=1.0, stream=None):
+    def __init__(self, shape, dt=0.1, M=1.0, kappa=1.0, h=1.0, stream=None, model="ch"):
         self.shape = tuple(int(s) for s in shape)
         self.params = Params(dt, M, kappa, h)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -99,6 +105,8 @@ class Grid:
         if s != EVX_OK:
             raise EvxError(s, lib.evx_last_error(None).decode())
         self._h = h_
+        if model != "ch":
+            self.set_model(model)
 
     # -- helpers
     def _ck(self, s):
@@ -152,8 +160,18 @@ class Grid:
         self._ck(lib.evx_get_field_host(self._h, ctypes.c_void_p(out.data_ptr())))
         return out
 
+    def set_model(self, model):
+        if model not in MODELS:
+            raise ValueError("model must be one of %s" % sorted(MODELS))
+        self._ck(lib.evx_set_model(self._h, MODELS[model]))
+
+    @property
+    def model(self):
+        m = lib.evx_get_model(self._h)
+        return {v: k for k, v in MODELS.items()}[m]
+
     def step(self, n=1):
-        self._ck(lib.evx_ch_step(self._h, int(n)))
+        self._ck(lib.evx_step(self._h, int(n)))
 
     def energy(self):
         E = ctypes.c_double()

@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--train-iters", type=int, default=200)
+    ap.add_argument("--ac-steps", type=int, default=50, help="Allen-Cahn steps timed after the CH run (0: skip)")
     ap.add_argument("--conv-probe", default=None, metavar="B,X,Y,Z",
                     help="only time the surrogate's 32->32 convolution (plain epilogue) on this shape and exit")
     return ap.parse_args()
@@ -384,7 +385,11 @@ def main():
 
     # roofline of the dominant pass
     names = ["x pass + k-space update", "y inverse", "z C2R + c^3-c + R2C", "y forward"]
-    kern = ["xupdate_kernel", "spass_kernel<1>", "zpass_kernel<Z_STEP>", "spass_kernel<-1>"]
+    fast = n in (64, 128, 256, 512, 1024) and os.environ.get("EVX_GENERIC", "") != "1"
+    tp = max(n // 32, 2)
+    kern = (["fast::fxupd_tma_kernel<%d>" % tp, "fast::fspass_tma_kernel<%d, 1>" % tp,
+             "fast::fzstep_kernel<%d, 128>" % max(tp // 2, 2), "fast::fspass_tma_kernel<%d, -1>" % tp] if fast else
+            ["xupdate_kernel", "spass_kernel<1>", "zpass_kernel<Z_STEP>", "spass_kernel<-1>"])
     dom = max(range(4), key=lambda k: pass_ms[k])
     avg_ms = pass_ms[dom] / max(pass_cnt[dom], 1)
     alg_bytes = g.pass_bytes(dom)
@@ -414,6 +419,25 @@ def main():
                "job": "pinned host c0 -> evx_set_field_host -> %d steps -> evx_get_field_host; "
                       "the field's bytes are spread over the job's steps" % args.steps}
         del host_in, host_out
+    # ---- the Allen-Cahn model on the same engine and grid (device-resident)
+    ac = None
+    if args.ac_steps > 0:
+        g.set_model("ac")
+        g.set_field(c0_dev)
+        g.step(3)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step(args.ac_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t_ac = max_over_ranks(e0.elapsed_time(e1))
+        ac = {"workload": "Allen-Cahn %d^3, same c0, dt 0.1, L = kappa = 1, %d steps (after 3 warm-up)"
+                          % (n, args.ac_steps),
+              "value": job_throughput(ws, args.ac_steps, V, t_ac * 1e-3), "unit": UNIT,
+              "ms_per_step": t_ac / args.ac_steps, "launches_per_step": 5, "mean_after": g.mean()}
+        g.set_model("ch")
     fp = g.footprint()
     g.close()
     del c0_dev
@@ -459,6 +483,7 @@ def main():
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": 4 * args.steps,
+        "allen_cahn": ac,
         "surrogate": sur,
     }
     print(json.dumps(out), flush=True)

@@ -122,7 +122,26 @@ evx_status evx_ch_step(evx_grid *g, int n_steps);
  * Same four passes (plus a one-block mean update), same sizes, energy and
  * field calls; evx_ch_adjoint and evx_ch_step_static are Cahn-Hilliard only.
  * Changing the model drops the captured step graphs (synchronises). */
-typedef enum { EVX_MODEL_CH = 0, EVX_MODEL_AC = 1 } evx_model;
+/*
+ * EVX_MODEL_VM: Cahn-Hilliard with the variable mobility of Eq.
+ * (cahn-hilliard), M(phi) = D0 phi (1 - phi), read in the c form as
+ * M(c) = p.M max(1 - c^2, 0), in the general form of subsection
+ * "Semi-implicit timestepping": the right-hand side is a finite-difference
+ * approximation in real space and only the preconditioner is spectral,
+ *   c' = c + F^-1{ dt / (1 + dt M kappa |k|^4) F{div(M(c) grad mu)} },
+ *   mu = c^3 - c - kappa lap_h c,
+ * with second-order central differences in conservative form (7-point
+ * Laplacian; face mobility (M_i + M_j)/2). The state is the real FP32 field;
+ * per step two FD stencil kernels, a z R2C, the y and x passes (x pass in its
+ * preconditioner-only mode), the y inverse and a z C2R that adds the increment
+ * (7 launches). Switching to or from EVX_MODEL_VM drops the field (set it
+ * again); it allocates one more real field for the right-hand side. Its
+ * energy is the FD form h^3 sum (c^2-1)^2/4 + h^3 (kappa/2) sum_d |D_d c|^2
+ * and evx_mean sums the field in FP64 on each call. Per-pass times in this
+ * model: 0 x preconditioner + y inverse + z C2R-add, 1 FD stencils,
+ * 2 z R2C, 3 y forward.
+ */
+typedef enum { EVX_MODEL_CH = 0, EVX_MODEL_AC = 1, EVX_MODEL_VM = 2 } evx_model;
 evx_status evx_set_model(evx_grid *g, int model);
 int evx_get_model(const evx_grid *g); /* -1 for NULL */
 

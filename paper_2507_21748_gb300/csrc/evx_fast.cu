@@ -383,8 +383,10 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
     if (threadIdx.x == 0) bulk_wait0();
 }
 
-// x pass + update with TMA: boxes {8, 1, BOX (x), 1}
-template <int TP, bool AC>
+// x pass + update with TMA: boxes {8, 1, BOX (x), 1}. MODE 0: Cahn-Hilliard,
+// 1: Allen-Cahn, 2: preconditioner only (S' = F_x^-1 (dt / (1 + dt M0 kappa |k|^4)
+// F_x W), S not read; the variable-mobility model's spectral step)
+template <int TP, int MODE>
 __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int ntiles,
                                                               const __grid_constant__ CUtensorMap mW,
                                                               const __grid_constant__ CUtensorMap mS,
@@ -418,9 +420,10 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         for (int b = 0; b < NBOX; ++b)
             tma_load4(buf + b * BOX * 8, m, chunk * 8, ky % YB, b * BOX, ky / YB, bar);
     };
+    constexpr bool AC = MODE == 1, PRE = MODE == 2;
     if (threadIdx.x == 0) {
         issue(&mW, bufW, bars + 0, tile);
-        issue(&mS, bufS, bars + 1, tile);
+        if (!PRE) issue(&mS, bufS, bars + 1, tile);
     }
     uint32_t parity = 0;
     const float ndtM = -a.dtM;
@@ -451,34 +454,43 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) {
-                const float f = AC ? ndtM : ndtM * (k2xs[n2 * NB + i + 32 * c] + k2yz);
+                const float k2g = k2xs[n2 * NB + i + 32 * c] + k2yz;
+                const float f = PRE  ? a.dtM * a.invL * rcp_approx(fmaf(a.dtMk, k2g * k2g, 1.f))
+                                : AC ? ndtM
+                                     : ndtM * k2g;
                 G[i * TP + c] = cscale(v[i * TP + c], f);
             }
-        // ---- c_hat = F_x S
-        ok = mbar_wait(bars + 1, parity);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
-            break;
-        }
-        parity ^= 1;
+        if (PRE) {
+            parity ^= 1;
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufS[(n2 + TP * n1) * 8 + p];
-        __syncthreads();
-        if (threadIdx.x == 0 && next < ntiles) issue(&mS, bufS, bars + 1, next);
-        Dft<32, -1>::run(v);
-        twiddle_a<TP, -1>(v, n2, tA);
-        t1_s<TP, 8>(v, xb, n2, p);
-        pass_b<TP, -1>(v);
-        // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L; k = 0 stays out
-        //      (Allen-Cahn: (c_hat - dt L g_hat) / (1 + dt L kappa |k|^2) / L)
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-#pragma unroll
-            for (int c = 0; c < TP; ++c) {
-                const float k2 = k2xs[n2 * NB + i + 32 * c] + k2yz;
-                const float f = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
-                v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), f);
+            for (int q = 0; q < 32; ++q) v[q] = G[q];
+        } else {
+            // ---- c_hat = F_x S
+            ok = mbar_wait(bars + 1, parity);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
+                break;
             }
+            parity ^= 1;
+#pragma unroll
+            for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufS[(n2 + TP * n1) * 8 + p];
+            __syncthreads();
+            if (threadIdx.x == 0 && next < ntiles) issue(&mS, bufS, bars + 1, next);
+            Dft<32, -1>::run(v);
+            twiddle_a<TP, -1>(v, n2, tA);
+            t1_s<TP, 8>(v, xb, n2, p);
+            pass_b<TP, -1>(v);
+            // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L; k = 0 stays out
+            //      (Allen-Cahn: (c_hat - dt L g_hat) / (1 + dt L kappa |k|^2) / L)
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+#pragma unroll
+                for (int c = 0; c < TP; ++c) {
+                    const float k2 = k2xs[n2 * NB + i + 32 * c] + k2yz;
+                    const float f = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
+                    v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), f);
+                }
+        }
         if (ky == 0 && kz == 0 && n2 == 0) v[0] = make_float2(0.f, 0.f);
         // ---- S' = F_x^-1 c_hat'
         pass_b<TP, 1>(v);
@@ -636,7 +648,9 @@ static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) 
         return false;
     const size_t smem = sizeof(float2) * (2 * L * 8 + (L + TP) * 8 + 2 * L) + sizeof(float) * L + 16;
     int per = 0;
-    auto kern = a.model == 1 ? fast::fxupd_tma_kernel<TP, true> : fast::fxupd_tma_kernel<TP, false>;
+    auto kern = a.model == 2   ? fast::fxupd_tma_kernel<TP, 2>
+                : a.model == 1 ? fast::fxupd_tma_kernel<TP, 1>
+                               : fast::fxupd_tma_kernel<TP, 0>;
     cudaError_t e = prep(kern, smem, 8 * TP, &per);
     if (e != cudaSuccess) {
         *err = e;

@@ -19,6 +19,7 @@ struct evx_grid {
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
     float2* S = nullptr;
     float2* W = nullptr;
+    float* R = nullptr;          // variable-mobility model: real right-hand side (V floats)
     double* d_scal = nullptr;    // [0] cbar, [1] bulk energy, [2] gradient energy, [3..7] scratch
     double* d_part = nullptr;
     int npart = 0;

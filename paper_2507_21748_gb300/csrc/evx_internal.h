@@ -56,6 +56,8 @@ struct XUpdArgs {
     float dtM, dtMk, invL;
     int model;          // 0 Cahn-Hilliard: b = -dt M |k|^2, D = 1 + dt M kappa |k|^4
                         // 1 Allen-Cahn:    b = -dt L,       D = 1 + dt L kappa |k|^2
+                        // 2 preconditioner: S_out = F_x^-1 dt / (1 + dtMk |k|^4) F_x W / L,
+                        //   S not read (dtM holds dt)
 };
 
 // Energy: gradient term sum_k w(kz) |k|^2 |c_hat|^2 from the state S.
@@ -95,6 +97,7 @@ struct ZPassArgs {
     const double* cbar;     // FP64 mean (Z_STEP, Z_C2R); may be null (0)
     double* partials;       // bulk energy partial per CTA (Z_C2R) or null
     double* gsum;           // Z_STEP, Allen-Cahn: per-CTA FP64 sums of g(c) - g(cbar), or null
+    int accumulate;         // Z_C2R: rout += value instead of rout = value
     // map_rows = 1: real rows rin / rout are a caller's C-order field; memory
     // row r of the y-blocked spectrum is caller row x * ny + y
     int map_rows, YB, nxr, nyr;
@@ -109,6 +112,16 @@ cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st);
 cudaError_t launch_xupdate(const XUpdArgs& a, cudaStream_t st);
 cudaError_t launch_xenergy(const XEnergyArgs& a, cudaStream_t st);
 cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st, int* grid_used = nullptr);
+// variable-mobility model (real C-order fields, z fastest; periodic)
+//   mu  = c^3 - c - (kappa / h^2) lap1 c                    (lap1: 7-point stencil, h = 1)
+//   rhs = (1 / h^2) sum over the 6 neighbours j of (M_i + M_j)/2 (mu_j - mu_i), M = M0 max(1 - c^2, 0)
+//   partials[b] = sum over the CTA's voxels of (c^2 - 1)^2 / 4 + (kappa / 2h^2) sum_d (c_{i+e_d} - c_i)^2
+cudaError_t launch_vm_mu(const float* c, float* mu, int nx, int ny, int nz, float kappa_h2, cudaStream_t st);
+cudaError_t launch_vm_rhs(const float* c, const float* mu, float* rhs, int nx, int ny, int nz, float M0,
+                          float inv_h2, cudaStream_t st);
+cudaError_t launch_vm_energy(const float* c, int nx, int ny, int nz, double kappa_2h2, double* partials, int nparts,
+                             cudaStream_t st);
+int vm_energy_grid(int nx, int ny, int nparts);  // partials the energy launch writes
 // Allen-Cahn mean: cbar <- cbar - dtL (g(cbar) + sum(gsum[0..n)) / V), one block, fixed order
 cudaError_t launch_ac_mean(const double* gsum, int n, double* cbar, double dtL, double invV, cudaStream_t st);
 int zpass_grid(const ZPassArgs& a);

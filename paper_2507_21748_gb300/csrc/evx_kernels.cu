@@ -15,6 +15,8 @@
 #include <cstdint>
 #include <cstdlib>
 
+#include <algorithm>
+
 #include "evx_internal.h"
 
 namespace evx {
@@ -113,11 +115,12 @@ __global__ void __launch_bounds__(NT, 1) xupdate_kernel(XUpdArgs a) {
     const int col0 = chunk * SP;
     const long long base = split_off(ky, a.YB, a.os, a.os2) + col0;
     const bool haveW = a.W != nullptr;
+    const bool pre = a.model == 2;  // preconditioner only: S' = F_x^-1 (dt / (1 + dt M0 kappa |k|^4)) F_x W
     if (haveW) load_x_cols(tile, 0, a.W, base, a.rs, L, col0, a.ncols);
-    load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols);
+    if (!pre) load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols);
     __syncthreads();
     if (haveW) fft_cols<-1>(tile, L, 2 * SP, a.plan, tws);
-    fft_cols<-1>(tile + SP, L, 2 * SP, a.plan, tws);
+    if (!pre) fft_cols<-1>(tile + SP, L, 2 * SP, a.plan, tws);
     const float k2y = a.k2y[ky];
     for (int e = threadIdx.x; e < L * SP; e += NT) {
         const int i = e / SP, p = e % SP;
@@ -128,9 +131,12 @@ __global__ void __launch_bounds__(NT, 1) xupdate_kernel(XUpdArgs a) {
             // Allen-Cahn:   a = 1/D, b = -dt L / D,       D = 1 + dt L kappa |k|^2
             const float ainv = a.invL / fmaf(a.dtMk, a.model == 1 ? k2 : k2 * k2, 1.f);
             const float b = -a.dtM * (a.model == 1 ? 1.f : k2) * ainv;
-            const float2 c = tile[i * (2 * SP) + SP + p];
+            const float2 c = pre ? make_float2(0.f, 0.f) : tile[i * (2 * SP) + SP + p];
             float2 r = make_float2(ainv * c.x, ainv * c.y);
-            if (haveW) {
+            if (pre) {  // dtM holds dt here: r = dt / (1 + dt M0 kappa |k|^4) g_hat / L
+                const float2 gh = tile[i * (2 * SP) + p];
+                r = make_float2(a.dtM * ainv * gh.x, a.dtM * ainv * gh.y);
+            } else if (haveW) {
                 const float2 gh = tile[i * (2 * SP) + p];
                 r.x = fmaf(b, gh.x, r.x);
                 r.y = fmaf(b, gh.y, r.y);
@@ -277,8 +283,15 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
                     if (a.gsum) acc += (double)gv.x + (double)gv.y;
                 } else {  // Z_C2R
                     const long long rr = a.map_rows ? user_row(row0 + r, a.YB, a.nxr, a.nyr) : row0 + r;
-                    if (a.rout)
-                        reinterpret_cast<float2*>(a.rout + rr * a.rpitch)[n] = make_float2(c0, c1);
+                    if (a.rout) {
+                        float2* o = reinterpret_cast<float2*>(a.rout + rr * a.rpitch) + n;
+                        if (a.accumulate) {  // the variable-mobility step adds its increment
+                            const float2 prev = *o;
+                            *o = make_float2(prev.x + c0, prev.y + c1);
+                        } else {
+                            *o = make_float2(c0, c1);
+                        }
+                    }
                     if (a.partials) {
                         const double q0 = (double)c0 * c0 - 1.0, q1 = (double)c1 * c1 - 1.0;
                         acc += q0 * q0 + q1 * q1;
@@ -349,6 +362,81 @@ __global__ void __launch_bounds__(1024) reduce_partials_kernel(const double* par
     for (int i = threadIdx.x; i < n; i += 1024) acc += partials[i];
     acc = block_sum_double(acc, ws);
     if (threadIdx.x == 0) *out = acc * scale;
+}
+
+// ------------------------------------------- variable-mobility FD stencils
+// Real C-order fields (x, y, z), z fastest, periodic. A CTA walks (x, y) rows
+// (grid-stride); its threads run along z, so every neighbour row is read
+// coalesced. Rows r and r + 1 (y neighbours) and r +- ny (x neighbours) are
+// processed by CTAs running at the same time, so the re-reads hit L2.
+struct VmRow {
+    long long base, xp, xm, yp, ym;
+};
+__device__ __forceinline__ VmRow vm_row(long long row, int nx, int ny, int nz) {
+    const int x = (int)(row / ny), y = (int)(row - (long long)x * ny);
+    VmRow r;
+    r.base = row * nz;
+    r.xp = ((long long)(x + 1 == nx ? 0 : x + 1) * ny + y) * nz;
+    r.xm = ((long long)(x == 0 ? nx - 1 : x - 1) * ny + y) * nz;
+    r.yp = ((long long)x * ny + (y + 1 == ny ? 0 : y + 1)) * nz;
+    r.ym = ((long long)x * ny + (y == 0 ? ny - 1 : y - 1)) * nz;
+    return r;
+}
+
+// mu = c^3 - c - (kappa / h^2) (sum of the 6 neighbours - 6 c)
+__global__ void __launch_bounds__(256) vm_mu_kernel(const float* __restrict__ c, float* __restrict__ mu, int nx,
+                                                     int ny, int nz, float kh2) {
+    const long long nrows = (long long)nx * ny;
+    for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const VmRow r = vm_row(row, nx, ny, nz);
+        for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+            const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
+            const float v = c[r.base + z];
+            const float nb = ((c[r.xp + z] + c[r.xm + z]) + (c[r.yp + z] + c[r.ym + z])) +
+                             (c[r.base + zp] + c[r.base + zm]);
+            mu[r.base + z] = v * (v * v - 1.f) - kh2 * fmaf(-6.f, v, nb);
+        }
+    }
+}
+
+// rhs = (1 / h^2) sum_j (M_i + M_j)/2 (mu_j - mu_i), M = M0 max(1 - c^2, 0)
+__global__ void __launch_bounds__(256) vm_rhs_kernel(const float* __restrict__ c, const float* __restrict__ mu,
+                                                      float* __restrict__ rhs, int nx, int ny, int nz, float M0,
+                                                      float ih2) {
+    const long long nrows = (long long)nx * ny;
+    auto mob = [&](float v) { return M0 * fmaxf(1.f - v * v, 0.f); };
+    for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const VmRow r = vm_row(row, nx, ny, nz);
+        for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+            const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
+            const long long idx[6] = {r.xp + z, r.xm + z, r.yp + z, r.ym + z, r.base + zp, r.base + zm};
+            const float mi = mob(c[r.base + z]), ui = mu[r.base + z];
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc = fmaf(0.5f * (mi + mob(c[idx[q]])), mu[idx[q]] - ui, acc);
+            rhs[r.base + z] = acc * ih2;
+        }
+    }
+}
+
+// FD energy partials: (c^2 - 1)^2 / 4 + (kappa / 2h^2) sum_d (c_{i+e_d} - c_i)^2 per voxel, FP64
+__global__ void __launch_bounds__(256) vm_energy_kernel(const float* __restrict__ c, int nx, int ny, int nz,
+                                                         double k2h2, double* partials) {
+    __shared__ double ws[32];
+    const long long nrows = (long long)nx * ny;
+    double acc = 0.0;
+    for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const VmRow r = vm_row(row, nx, ny, nz);
+        for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+            const int zp = z + 1 == nz ? 0 : z + 1;
+            const double v = c[r.base + z];
+            const double q = v * v - 1.0;
+            const double dx = c[r.xp + z] - v, dy = c[r.yp + z] - v, dz = c[r.base + zp] - v;
+            acc += 0.25 * q * q + k2h2 * (dx * dx + dy * dy + dz * dz);
+        }
+    }
+    acc = block_sum_double(acc, ws);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
 // Allen-Cahn: the k = 0 mode of the update has D = 1, so the FP64 mean moves by
@@ -468,6 +556,40 @@ cudaError_t launch_sum_field(const float* c, long long nrows, int rowlen, long l
     sum_rows_kernel<<<nblocks, NT, 0, st>>>(c, nrows, rowlen, pitch, partials);
     return cudaGetLastError();
 }
+
+static int vm_grid(int nx, int ny) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const long long nrows = (long long)nx * ny;
+    return (int)std::min<long long>(nrows, 8LL * sms);
+}
+
+cudaError_t launch_vm_mu(const float* c, float* mu, int nx, int ny, int nz, float kappa_h2, cudaStream_t st) {
+    vm_mu_kernel<<<vm_grid(nx, ny), 256, 0, st>>>(c, mu, nx, ny, nz, kappa_h2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vm_rhs(const float* c, const float* mu, float* rhs, int nx, int ny, int nz, float M0,
+                          float inv_h2, cudaStream_t st) {
+    vm_rhs_kernel<<<vm_grid(nx, ny), 256, 0, st>>>(c, mu, rhs, nx, ny, nz, M0, inv_h2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vm_energy(const float* c, int nx, int ny, int nz, double kappa_2h2, double* partials, int nparts,
+                             cudaStream_t st) {
+    const int grid = std::min(vm_grid(nx, ny), nparts);
+    vm_energy_kernel<<<grid, 256, 0, st>>>(c, nx, ny, nz, kappa_2h2, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return grid > 0 ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int vm_energy_grid(int nx, int ny, int nparts) { return std::min(vm_grid(nx, ny), nparts); }
 
 cudaError_t launch_ac_mean(const double* gsum, int n, double* cbar, double dtL, double invV, cudaStream_t st) {
     ac_mean_kernel<<<1, 1024, 0, st>>>(gsum, n, cbar, dtL, invV);

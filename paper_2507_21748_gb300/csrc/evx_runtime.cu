@@ -181,7 +181,45 @@ using namespace evxrt;
 
 // --------------------------------------------------------- step sequence
 // ev: null, or 5 events recorded around the four passes
+// variable mobility: c (real, in S) <- c + F^-1{ dt / (1 + dt M kappa |k|^4) F{div(M(c) grad mu)} }
+// events: [FD stencils] [z R2C] [y forward] [x preconditioner + y inverse + z C2R-add]
+static cudaError_t issue_vm_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) {
+    cudaError_t e;
+    float* c = reinterpret_cast<float*>(g->S);
+    float* mu = reinterpret_cast<float*>(g->W);
+    const double ih2 = 1.0 / (g->p.h * g->p.h);
+    if (ev) cudaEventRecord(ev[0], st);
+    if ((e = launch_vm_mu(c, mu, g->nx, g->ny, g->nz, (float)(g->p.kappa * ih2), st)) != cudaSuccess) return e;
+    if ((e = launch_vm_rhs(c, mu, g->R, g->nx, g->ny, g->nz, (float)g->p.M, (float)ih2, st)) != cudaSuccess)
+        return e;
+    if (ev) cudaEventRecord(ev[1], st);
+    ZPassArgs z = z_args(g);
+    z.rin = g->R;
+    z.rpitch = g->nz;
+    z.map_rows = 1;
+    z.out = g->W;
+    if ((e = launch_zpass(z, Z_R2C, st)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], st);
+    if ((e = launch_spass(y_args(g, g->W, g->W), -1, st)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], st);
+    XUpdArgs xa = x_args(g, g->W, g->W, g->W, g->p.dt, g->p.M, g->p.kappa);
+    xa.model = 2;
+    xa.dtM = (float)g->p.dt;  // preconditioner numerator
+    if ((e = launch_xupdate(xa, st)) != cudaSuccess) return e;
+    if ((e = launch_spass(y_args(g, g->W, g->W), +1, st)) != cudaSuccess) return e;
+    ZPassArgs z2 = z_args(g);
+    z2.in = g->W;
+    z2.rout = c;
+    z2.rpitch = g->nz;
+    z2.map_rows = 1;
+    z2.accumulate = 1;
+    if ((e = launch_zpass(z2, Z_C2R, st)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[4], st);
+    return cudaSuccess;
+}
+
 static cudaError_t issue_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) {
+    if (g->model == EVX_MODEL_VM) return issue_vm_step(g, st, ev);
     cudaError_t e;
     if (ev) cudaEventRecord(ev[0], st);
     if ((e = launch_spass(y_args(g, g->S, g->W), +1, st)) != cudaSuccess) return e;
@@ -342,7 +380,7 @@ evx_status evx_grid_destroy(evx_grid* g) {
     if (g->st || g->S) cudaStreamSynchronize(g->st);
     evxrt::adjoint_free(g);
     drop_graphs(g);
-    for (auto ptr : {(void*)g->S, (void*)g->W, (void*)g->d_scal, (void*)g->d_part, (void*)g->twx,
+    for (auto ptr : {(void*)g->S, (void*)g->W, (void*)g->R, (void*)g->d_scal, (void*)g->d_part, (void*)g->twx,
                      (void*)g->twy, (void*)g->twz, (void*)g->rtw, (void*)g->k2x, (void*)g->k2y,
                      (void*)g->k2z})
         if (ptr) cudaFree(ptr);
@@ -394,9 +432,16 @@ static evx_status load_real(evx_grid* g, const float* rows, long long pitch, int
     return EVX_OK;
 }
 
+static size_t field_bytes(const evx_grid* g) { return sizeof(float) * (size_t)g->nx * g->ny * g->nz; }
+
 evx_status evx_set_field(evx_grid* g, const float* d_c) {
     if (!g || !d_c) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!aligned8(d_c)) return fail(g, EVX_ERR_ARG, "field pointer must be 8-byte aligned");
+    if (g->model == EVX_MODEL_VM) {  // the variable-mobility state is the real field itself
+        CK(cudaMemcpyAsync(g->S, d_c, field_bytes(g), cudaMemcpyDeviceToDevice, g->st));
+        g->has_field = true;
+        return EVX_OK;
+    }
     return load_real(g, d_c, g->nz, 1);
 }
 
@@ -422,6 +467,12 @@ static evx_status host_rows_copy(evx_grid* g, float* host, bool to_device) {
 
 evx_status evx_set_field_host(evx_grid* g, const float* h_c) {
     if (!g || !h_c) return fail(g, EVX_ERR_ARG, "NULL argument");
+    if (g->model == EVX_MODEL_VM) {
+        CK(cudaMemcpyAsync(g->S, h_c, field_bytes(g), cudaMemcpyHostToDevice, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        g->has_field = true;
+        return EVX_OK;
+    }
     evx_status s = host_rows_copy(g, const_cast<float*>(h_c), true);
     if (s != EVX_OK) return s;
     s = load_real(g, (const float*)g->W, 2LL * g->Zp, 0);
@@ -449,12 +500,21 @@ evx_status evx_get_field(evx_grid* g, float* d_out) {
     if (!g || !d_out) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     if (!aligned8(d_out)) return fail(g, EVX_ERR_ARG, "output pointer must be 8-byte aligned");
+    if (g->model == EVX_MODEL_VM) {
+        CK(cudaMemcpyAsync(d_out, g->S, field_bytes(g), cudaMemcpyDeviceToDevice, g->st));
+        return EVX_OK;
+    }
     return store_real(g, d_out, g->nz, nullptr, 1);
 }
 
 evx_status evx_get_field_host(evx_grid* g, float* h_out) {
     if (!g || !h_out) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    if (g->model == EVX_MODEL_VM) {
+        CK(cudaMemcpyAsync(h_out, g->S, field_bytes(g), cudaMemcpyDeviceToHost, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        return check_timeouts(g);
+    }
     evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, nullptr, 0);
     if (s != EVX_OK) return s;
     s = host_rows_copy(g, h_out, false);
@@ -465,10 +525,21 @@ evx_status evx_get_field_host(evx_grid* g, float* h_out) {
 
 evx_status evx_set_model(evx_grid* g, int model) {
     if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
-    if (model != EVX_MODEL_CH && model != EVX_MODEL_AC) return fail(g, EVX_ERR_ARG, "unknown model %d", model);
+    if (model != EVX_MODEL_CH && model != EVX_MODEL_AC && model != EVX_MODEL_VM)
+        return fail(g, EVX_ERR_ARG, "unknown model %d", model);
     if (model != g->model) {
         CK(cudaStreamSynchronize(g->st));
         drop_graphs(g);
+        if (model == EVX_MODEL_VM && !g->R) {
+            if (cudaMalloc(&g->R, field_bytes(g)) != cudaSuccess) {
+                cudaGetLastError();
+                g->R = nullptr;
+                return fail(g, EVX_ERR_OOM, "out of device memory for the right-hand-side buffer");
+            }
+            g->bytes += field_bytes(g);
+        }
+        // CH and AC share the spectral state; the variable-mobility state is the real field
+        if (model == EVX_MODEL_VM || g->model == EVX_MODEL_VM) g->has_field = false;
         g->model = model;
     }
     return EVX_OK;
@@ -523,11 +594,36 @@ evx_status evx_step(evx_grid* g, int n_steps) {
     return EVX_OK;
 }
 
+// variable mobility: FP64 mean of the real field -> d_scal[0]
+static cudaError_t vm_sum(evx_grid* g) {
+    const long long nrows = (long long)g->nx * g->ny;
+    const double V = (double)nrows * g->nz;
+    cudaError_t e = launch_sum_field(reinterpret_cast<const float*>(g->S), nrows, g->nz, g->nz, g->d_part,
+                                     SUM_BLOCKS, g->st);
+    if (e != cudaSuccess) return e;
+    return launch_reduce_partials(g->d_part, SUM_BLOCKS, g->d_scal + 0, 1.0 / V, g->st);
+}
+
 evx_status evx_energy(evx_grid* g, double* E, double* mass) {
     if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     const double h3 = g->p.h * g->p.h * g->p.h;
     const double V = (double)g->nx * g->ny * g->nz;
+    if (g->model == EVX_MODEL_VM) {  // FD energy of the real field, h^3 sum (...)
+        const float* c = reinterpret_cast<const float*>(g->S);
+        const double k2h2 = 0.5 * g->p.kappa / (g->p.h * g->p.h);
+        CK(launch_vm_energy(c, g->nx, g->ny, g->nz, k2h2, g->d_part, g->npart, g->st));
+        CK(launch_reduce_partials(g->d_part, vm_energy_grid(g->nx, g->ny, g->npart), g->d_scal + 1, h3, g->st));
+        CK(vm_sum(g));
+        double host[2];
+        CK(cudaMemcpyAsync(host, g->d_scal, sizeof host, cudaMemcpyDeviceToHost, g->st));
+        CK(cudaStreamSynchronize(g->st));
+        if (!std::isfinite(host[1]) || !std::isfinite(host[0]))
+            return fail(g, EVX_ERR_NONFINITE, "field holds NaN or Inf (energy %g, mean %g)", host[1], host[0]);
+        if (E) *E = host[1];
+        if (mass) *mass = h3 * V * host[0];
+        return check_timeouts(g);
+    }
     // bulk: h^3/4 sum (c^2-1)^2 over the real field (written into W's row slots, discarded)
     evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, g->d_part, 0);
     if (s != EVX_OK) return s;
@@ -570,6 +666,7 @@ evx_status evx_energy(evx_grid* g, double* E, double* mass) {
 evx_status evx_mean(evx_grid* g, double* cbar) {
     if (!g || !cbar) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    if (g->model == EVX_MODEL_VM) CK(vm_sum(g));  // the real field's FP64 mean (not carried)
     CK(cudaMemcpyAsync(cbar, g->d_scal, sizeof(double), cudaMemcpyDeviceToHost, g->st));
     CK(cudaStreamSynchronize(g->st));
     return check_timeouts(g);

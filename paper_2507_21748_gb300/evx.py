@@ -24,7 +24,7 @@ EXPORTS = [
     "evx_mean", "evx_ch_adjoint", "evx_footprint", "evx_set_profiling", "evx_pass_times",
     "evx_pass_bytes", "evx_ch_step_static", "evx_set_model", "evx_get_model", "evx_step", "evx_last_error",
 ]
-MODELS = {"ch": 0, "ac": 1}  # evx_model: Cahn-Hilliard, Allen-Cahn
+MODELS = {"ch": 0, "ac": 1, "vm": 2}  # evx_model: Cahn-Hilliard, Allen-Cahn, variable-mobility CH
 
 
 class EvxError(RuntimeError):
@@ -93,8 +93,9 @@ def _check_field(t, shape):
 
 class Grid:
     """A periodic nx*ny*nz grid owned by libevx, stepping the Cahn-Hilliard model
-    (``model="ch"``, default) or the Allen-Cahn model (``model="ac"``, M is then
-    the kinetic coefficient L)."""
+    (``model="ch"``, default), the Allen-Cahn model (``model="ac"``, M is then
+    the kinetic coefficient L) or Cahn-Hilliard with variable mobility
+    M max(1 - c^2, 0) and a finite-difference right-hand side (``model="vm"``)."""
 
     def __init__(self, shape, dt=0.1, M=1.0, kappa=1.0, h=1.0, stream=None, model="ch"):
         self.shape = tuple(int(s) for s in shape)

@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--train-iters", type=int, default=200)
     ap.add_argument("--ac-steps", type=int, default=50, help="Allen-Cahn steps timed after the CH run (0: skip)")
+    ap.add_argument("--vm-steps", type=int, default=20,
+                    help="variable-mobility CH steps timed after the CH run (0: skip)")
+    ap.add_argument("--step-probe", default=None, metavar="NX,NY,NZ,STEPS",
+                    help="only run STEPS Cahn-Hilliard steps on an NX x NY x NZ grid and exit (for profilers)")
     ap.add_argument("--conv-probe", default=None, metavar="B,X,Y,Z",
                     help="only time the surrogate's 32->32 convolution (plain epilogue) on this shape and exit")
     return ap.parse_args()
@@ -332,12 +336,30 @@ def conv_probe(spec):
                       "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
 
 
+def step_probe(spec):
+    """Runs a few Cahn-Hilliard steps (same recipe as the bench) on one grid:
+    a small, self-contained case for profilers (4 kernels per step after the
+    set-field kernels)."""
+    import torch
+    from paper_2507_21748_gb300 import evx, inputs
+    nx, ny, nz, steps = (int(v) for v in spec.split(","))
+    c0 = torch.from_numpy(inputs.uniform_field((nx, ny, nz), seed=0, offset=0.3)).cuda()
+    g = evx.Grid((nx, ny, nz), dt=DT, M=MOB, kappa=KAPPA, h=H)
+    g.set_field(c0)
+    g.step(steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"step_probe": [nx, ny, nz, steps], "mean": g.mean()}), flush=True)
+    g.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.conv_probe:
         return conv_probe(args.conv_probe)
+    if args.step_probe:
+        return step_probe(args.step_probe)
     import torch
     ws, rank, local = dist_env()
     if ws > 1:
@@ -419,6 +441,7 @@ def main():
                "job": "pinned host c0 -> evx_set_field_host -> %d steps -> evx_get_field_host; "
                       "the field's bytes are spread over the job's steps" % args.steps}
         del host_in, host_out
+    fp = g.footprint()  # the Cahn-Hilliard workload's footprint (the VM model adds a buffer)
     # ---- the Allen-Cahn model on the same engine and grid (device-resident)
     ac = None
     if args.ac_steps > 0:
@@ -438,7 +461,26 @@ def main():
               "value": job_throughput(ws, args.ac_steps, V, t_ac * 1e-3), "unit": UNIT,
               "ms_per_step": t_ac / args.ac_steps, "launches_per_step": 5, "mean_after": g.mean()}
         g.set_model("ch")
-    fp = g.footprint()
+    # ---- variable-mobility Cahn-Hilliard (FD right-hand side, spectral preconditioner)
+    vm = None
+    if args.vm_steps > 0:
+        g.set_model("vm")
+        g.set_field(c0_dev)
+        g.step(2)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step(args.vm_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t_vm = max_over_ranks(e0.elapsed_time(e1))
+        vm = {"workload": "variable-mobility CH %d^3, M(c) = max(1 - c^2, 0), same c0, dt 0.1, kappa = 1, "
+                          "%d steps (after 2 warm-up)" % (n, args.vm_steps),
+              "value": job_throughput(ws, args.vm_steps, V, t_vm * 1e-3), "unit": UNIT,
+              "ms_per_step": t_vm / args.vm_steps, "launches_per_step": 7,
+              "footprint_bytes": g.footprint()}
+        g.set_model("ch")
     g.close()
     del c0_dev
     torch.cuda.empty_cache()
@@ -484,6 +526,7 @@ def main():
         "clocks": clk,
         "gpu_launches": 4 * args.steps,
         "allen_cahn": ac,
+        "variable_mobility": vm,
         "surrogate": sur,
     }
     print(json.dumps(out), flush=True)

@@ -260,6 +260,209 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
     }
 }
 
+// ----------------------------------------- z transforms alone (R2C, C2R)
+// The two halves of fzstep_kernel as kernels of their own, for the field
+// I/O of the spectral models and for the variable-mobility step: same tile
+// (RPC rows of M = nz/2 complex samples per CTA, one shared buffer for the
+// rows and the transpose), same four-step FFT and real-transform twiddles.
+// Real rows are the caller's C-order rows when a.map_rows (row r of the
+// y-blocked spectrum is caller row user_row(r)), pitch a.rpitch floats.
+
+// R2C: real rows (minus the FP64 mean when a.cbar) -> complex rows a.out
+template <int TP, int NTZ>
+__global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int ntiles) {
+    constexpr int M = 32 * TP, NB = 32 / TP, RPC = NTZ / TP, RS = M + TP;
+    extern __shared__ float4 smem4[];
+    const int Zp = a.Zp;
+    const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
+    float2* buf = reinterpret_cast<float2*>(smem4);  // [RPC][BS]
+    float2* tA = buf + RPC * BS;
+    float2* tB = tA + M;
+    float2* rtws = tB + M;
+    const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    fill_twiddles<TP>(tA, tB, a.tw, NTZ);
+    for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
+    auto issue = [&](int tl) {
+        const long long row0 = (long long)tl * RPC;
+        for (int e = threadIdx.x; e < RPC * (M / 2); e += NTZ) {  // 16-byte chunks: 4 floats
+            const int rr = e / (M / 2), q = e - rr * (M / 2);
+            const long long row = row0 + rr;
+            const bool ok = row < a.nrows;
+            const long long ur = a.map_rows ? user_row(row, a.YB, a.nxr, a.nyr) : row;
+            const float* src = ok ? a.rin + ur * a.rpitch + 4 * q : a.rin;
+            cp_async16(buf + rr * BS + 2 * q, src, ok ? 16 : 0);
+        }
+        cp_commit();
+    };
+    issue(tile);
+    const double cbd = a.cbar ? *a.cbar : 0.0;
+    const float hi = (float)cbd, lo = (float)(cbd - (double)hi);
+    const bool sub = a.cbar != nullptr;
+    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB; };
+    for (; tile < ntiles; tile += gridDim.x) {
+        const long long row0 = (long long)tile * RPC;
+        cp_wait<0>();
+        __syncthreads();
+        // samples z[m] = c[2m] + i c[2m+1] in block ownership (m = n2 NB + i + 32 c)
+        float2 v[32];
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) {
+                float2 z = buf[r * BS + n2 * NB + i + 32 * c];
+                if (sub) {  // (x - hi) - lo: x - hi is exact for x within a factor 2 of hi
+                    z.x = (z.x - hi) - lo;
+                    z.y = (z.y - hi) - lo;
+                }
+                v[i * TP + c] = z;
+            }
+        __syncthreads();  // rows read: buf becomes transpose space
+        pass_b<TP, -1>(v);
+        twiddle_b<TP, -1>(v, n2, tB);
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) buf[slot(r, c, n2 * NB + i)] = v[i * TP + c];
+        __syncthreads();
+#pragma unroll
+        for (int aa = 0; aa < 32; ++aa) v[aa] = buf[slot(r, n2, aa)];
+        __syncthreads();  // buf free: fetch the next tile while this one finishes
+        if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
+        Dft<32, -1>::run(v);
+        // R2C post-processing from registers, partner by warp shuffle (as in the z step)
+        const long long row = row0 + r;
+        const bool rowok = row < a.nrows;
+        const int lane = threadIdx.x & 31;
+        const int src = (lane & ~(TP - 1)) | ((TP - n2) & (TP - 1));
+        float2* out = a.out + row * Zp;
+#pragma unroll
+        for (int d = 0; d < 32; ++d) {
+            float2 zm;
+            zm.x = __shfl_sync(0xffffffffu, v[31 - d].x, src);
+            zm.y = __shfl_sync(0xffffffffu, v[31 - d].y, src);
+            if (n2 == 0) zm = v[(32 - d) & 31];
+            const float2 zk = v[d];
+            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
+            const int k = n2 + TP * d;
+            if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
+        }
+        if (rowok && n2 == 0) out[M] = make_float2(v[0].x - v[0].y, 0.f);  // X_M = Re Z_0 - Im Z_0
+    }
+}
+
+// C2R: complex rows a.in -> real rows c = z / (ny nz) + cbar; ACC adds to the
+// rows instead; PART: FP64 partial per CTA of sum (c^2 - 1)^2 in a.partials
+template <int TP, int NTZ, bool ACC, bool PART>
+__global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int ntiles) {
+    constexpr int M = 32 * TP, NB = 32 / TP, RPC = NTZ / TP, RS = M + TP;
+    extern __shared__ float4 smem4[];
+    const int Zp = a.Zp, Zh = a.Zp / 2;
+    const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
+    float2* buf = reinterpret_cast<float2*>(smem4);  // [RPC][BS]
+    float2* tA = buf + RPC * BS;
+    float2* tB = tA + M;
+    float2* rtws = tB + M;
+    const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
+    int tile = blockIdx.x;
+    double acc = 0.0;
+    if (tile < ntiles) {
+        fill_twiddles<TP>(tA, tB, a.tw, NTZ);
+        for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
+    }
+    auto issue = [&](int tl) {
+        const long long row0 = (long long)tl * RPC;
+        for (int e = threadIdx.x; e < RPC * Zh; e += NTZ) {
+            const int rr = e / Zh, q = e - rr * Zh;
+            const bool ok = row0 + rr < a.nrows;
+            const float2* src = a.in + (row0 + rr) * Zp + 2 * q;
+            cp_async16(buf + rr * BS + 2 * q, ok ? src : a.in, ok ? 16 : 0);
+        }
+        cp_commit();
+    };
+    if (tile < ntiles) issue(tile);
+    const double cbd = a.cbar ? *a.cbar : 0.0;
+    const float cb = (float)cbd, cbl = (float)(cbd - (double)cb);
+    const float s = a.scale;
+    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB; };
+    for (; tile < ntiles; tile += gridDim.x) {
+        const long long row0 = (long long)tile * RPC;
+        cp_wait<0>();
+        __syncthreads();
+        // C2R pre-processing: Z[k] = (X_k + conj X_{M-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{M-k})
+        float2 v[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) {
+            const int k = n2 + TP * n1;
+            float2 xk = buf[r * BS + k], xm = buf[r * BS + (M - k)];
+            if (k == 0) {
+                xk.y = 0.f;
+                xm.y = 0.f;
+            }
+            const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
+            const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);
+            v[n1] = cadd(A, mul_i<1>(cmul(cconj(rtws[k]), B)));
+        }
+        __syncthreads();  // tile read: buf becomes transpose space
+        Dft<32, 1>::run(v);
+        twiddle_a<TP, 1>(v, n2, tA);
+#pragma unroll
+        for (int aa = 0; aa < 32; ++aa) buf[slot(r, n2, aa)] = v[aa];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) v[i * TP + c] = buf[slot(r, c, n2 * NB + i)];
+        pass_b<TP, 1>(v);
+        __syncthreads();  // transpose reads done: buf stages the real rows in natural order
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int c = 0; c < TP; ++c) {
+                const float2 z = v[i * TP + c];
+                buf[r * BS + n2 * NB + i + 32 * c] = make_float2(fmaf(z.x, s, cbl) + cb, fmaf(z.y, s, cbl) + cb);
+            }
+        __syncthreads();
+        for (int e = threadIdx.x; e < RPC * (M / 2); e += NTZ) {  // coalesced 16-byte stores
+            const int rr = e / (M / 2), q = e - rr * (M / 2);
+            const long long row = row0 + rr;
+            if (row >= a.nrows) continue;
+            const long long ur = a.map_rows ? user_row(row, a.YB, a.nxr, a.nyr) : row;
+            float4* dst = reinterpret_cast<float4*>(a.rout + ur * a.rpitch + 4 * q);
+            float4 val = *reinterpret_cast<const float4*>(buf + rr * BS + 2 * q);
+            if (ACC) {
+                const float4 prev = *dst;
+                val.x += prev.x;
+                val.y += prev.y;
+                val.z += prev.z;
+                val.w += prev.w;
+            }
+            *dst = val;
+            if (PART) {
+                const double q0 = (double)val.x * val.x - 1.0, q1 = (double)val.y * val.y - 1.0;
+                const double q2 = (double)val.z * val.z - 1.0, q3 = (double)val.w * val.w - 1.0;
+                acc += q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+            }
+        }
+        __syncthreads();  // staged rows stored: buf free for the next tile
+        if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
+    }
+    if (PART) {  // fixed-order CTA reduction
+        __shared__ double red[NTZ / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NTZ / 32; ++w) t += red[w];
+            a.partials[blockIdx.x] = t;
+        }
+    }
+}
+
 // ------------------------------------------------------------ TMA helpers
 // Tile loads and stores of the strided passes go through the tensor memory
 // accelerator: one thread issues cp.async.bulk.tensor boxes of up to 256 rows
@@ -703,6 +906,43 @@ static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st, int* grid_use
     if (grid_used) *grid_used = grid;
     kern<<<grid, NTZ, smem, st>>>(a, ntiles);
     return cudaGetLastError();
+}
+
+template <int TP>
+static cudaError_t run_fzconv(const ZPassArgs& a, int dir, cudaStream_t st, int* grid_used) {
+    constexpr int NTZ = 128, RPC = NTZ / TP, RS = 32 * TP + TP;
+    const int BS = TP + (((a.Zp > RS ? a.Zp : RS) - TP + 15) & ~15);  // as in the kernels
+    const size_t smem = sizeof(float2) * ((size_t)RPC * BS + 3 * 32 * TP + 1);
+    const int ntiles = (int)((a.nrows + RPC - 1) / RPC);
+    void (*kern)(ZPassArgs, int);
+    if (dir < 0)
+        kern = fast::fr2c_kernel<TP, NTZ>;
+    else if (a.accumulate)
+        kern = a.partials ? fast::fc2r_kernel<TP, NTZ, true, true> : fast::fc2r_kernel<TP, NTZ, true, false>;
+    else
+        kern = a.partials ? fast::fc2r_kernel<TP, NTZ, false, true> : fast::fc2r_kernel<TP, NTZ, false, false>;
+    int per = 0;
+    cudaError_t e = prep(kern, smem, NTZ, &per);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(ntiles, per * num_sms());
+    if (grid_used) *grid_used = grid;
+    kern<<<grid, NTZ, smem, st>>>(a, ntiles);
+    return cudaGetLastError();
+}
+
+// z R2C (dir < 0) or C2R (dir > 0) alone; false when the fast kernels do not apply
+bool fast_zconv(const ZPassArgs& a, int dir, cudaStream_t st, cudaError_t* err, int* grid_used) {
+    const int TP = tp_of(a.M);
+    if (TP < 2 || TP > 16) return false;
+    const float* real = dir < 0 ? a.rin : a.rout;
+    if (!real || ((uintptr_t)real & 15) || (a.rpitch & 3)) return false;
+    switch (TP) {
+        case 2: *err = run_fzconv<2>(a, dir, st, grid_used); return true;
+        case 4: *err = run_fzconv<4>(a, dir, st, grid_used); return true;
+        case 8: *err = run_fzconv<8>(a, dir, st, grid_used); return true;
+        case 16: *err = run_fzconv<16>(a, dir, st, grid_used); return true;
+    }
+    return false;
 }
 
 bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used) {

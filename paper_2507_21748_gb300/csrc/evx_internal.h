@@ -98,6 +98,7 @@ struct ZPassArgs {
     double* partials;       // bulk energy partial per CTA (Z_C2R) or null
     double* gsum;           // Z_STEP, Allen-Cahn: per-CTA FP64 sums of g(c) - g(cbar), or null
     int accumulate;         // Z_C2R: rout += value instead of rout = value
+    int fast_ok;            // Z_R2C / Z_C2R: the fast power-of-two kernels may run (grid then reported)
     // map_rows = 1: real rows rin / rout are a caller's C-order field; memory
     // row r of the y-blocked spectrum is caller row x * ny + y
     int map_rows, YB, nxr, nyr;
@@ -141,6 +142,7 @@ constexpr int SUM_BLOCKS = 1216;  // 8 x 152 SMs
 bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err);
 bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err);
 bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used);
+bool fast_zconv(const ZPassArgs& a, int dir, cudaStream_t st, cudaError_t* err, int* grid_used);
 bool fast_paths_enabled();  // false when the environment sets EVX_GENERIC=1
 // reads (and optionally clears) the flag a bounded TMA wait sets when it gives up
 bool fast_timeout_flag(int* flag, bool clear);

@@ -524,6 +524,9 @@ int zpass_grid(const ZPassArgs& a) {
 cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st, int* grid_used) {
     cudaError_t fe;
     if (mode == Z_STEP && fast_paths_enabled() && fast_zstep(a, st, &fe, grid_used)) return fe;
+    if ((mode == Z_R2C || mode == Z_C2R) && a.fast_ok && fast_paths_enabled() &&
+        fast_zconv(a, mode == Z_R2C ? -1 : 1, st, &fe, grid_used))
+        return fe;
     const size_t sm = zpass_smem(a.M, a.PZ, a.rows_per_cta);
     const int grid = zpass_grid(a);
     if (grid_used) *grid_used = grid;

@@ -198,6 +198,7 @@ static cudaError_t issue_vm_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) 
     z.rpitch = g->nz;
     z.map_rows = 1;
     z.out = g->W;
+    z.fast_ok = 1;
     if ((e = launch_zpass(z, Z_R2C, st)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
     if ((e = launch_spass(y_args(g, g->W, g->W), -1, st)) != cudaSuccess) return e;
@@ -213,6 +214,7 @@ static cudaError_t issue_vm_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) 
     z2.rpitch = g->nz;
     z2.map_rows = 1;
     z2.accumulate = 1;
+    z2.fast_ok = 1;
     if ((e = launch_zpass(z2, Z_C2R, st)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[4], st);
     return cudaSuccess;
@@ -424,6 +426,7 @@ static evx_status load_real(evx_grid* g, const float* rows, long long pitch, int
     z.map_rows = map;
     z.out = g->W;
     z.cbar = g->d_scal;  // transform c - cbar
+    z.fast_ok = 1;
     CK(launch_zpass(z, Z_R2C, g->st));
     CK(launch_spass(y_args(g, g->W, g->W), -1, g->st));
     // x pass with a = 1, b = 0: removes the k = 0 mode (carried in FP64)
@@ -483,7 +486,8 @@ evx_status evx_set_field_host(evx_grid* g, const float* h_c) {
 
 // state -> real rows (pitch floats apart), optional bulk-energy partials;
 // map as in load_real
-static evx_status store_real(evx_grid* g, float* rows, long long pitch, double* partials, int map) {
+static evx_status store_real(evx_grid* g, float* rows, long long pitch, double* partials, int map,
+                             int* grid_used = nullptr) {
     CK(launch_spass(y_args(g, g->S, g->W), +1, g->st));
     ZPassArgs z = z_args(g);
     z.in = g->W;
@@ -492,7 +496,10 @@ static evx_status store_real(evx_grid* g, float* rows, long long pitch, double* 
     z.map_rows = map;
     z.cbar = g->d_scal;
     z.partials = partials;
-    CK(launch_zpass(z, Z_C2R, g->st));
+    z.fast_ok = 1;
+    int zg = zpass_grid(z);
+    CK(launch_zpass(z, Z_C2R, g->st, &zg));
+    if (grid_used) *grid_used = zg;
     return EVX_OK;
 }
 
@@ -625,10 +632,10 @@ evx_status evx_energy(evx_grid* g, double* E, double* mass) {
         return check_timeouts(g);
     }
     // bulk: h^3/4 sum (c^2-1)^2 over the real field (written into W's row slots, discarded)
-    evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, g->d_part, 0);
+    int zg = 0;
+    evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, g->d_part, 0, &zg);
     if (s != EVX_OK) return s;
-    ZPassArgs z = z_args(g);
-    CK(launch_reduce_partials(g->d_part, zpass_grid(z), g->d_scal + 1, 0.25 * h3, g->st));
+    CK(launch_reduce_partials(g->d_part, zg, g->d_scal + 1, 0.25 * h3, g->st));
     // gradient: h^3 (kappa/2)(1/V) sum_k |k|^2 |c_hat|^2
     XEnergyArgs xa{};
     xa.S = g->S;

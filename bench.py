@@ -79,19 +79,41 @@ def replica_seed(rank: int) -> int:
     return rank
 
 
+def kernel_source(text, names):
+    """The definitions of the named functions in a C++ source (signature line
+    through the matching closing brace), concatenated: the part of a file a
+    kernel's memory traffic depends on."""
+    out = []
+    for name in names:
+        i = text.find(" " + name + "(")
+        if i < 0:
+            return None
+        i = text.rfind("\n", 0, text.rfind("template", 0, i) if "template" in text[max(0, i - 200):i] else i) + 1
+        j = text.index("{", text.index(name + "(", i))
+        depth = 0
+        for k in range(j, len(text)):
+            depth += {"{": 1, "}": -1}.get(text[k], 0)
+            if depth == 0:
+                out.append(text[i:k + 1])
+                break
+    return "\n".join(out)
+
+
 def measured_traffic(dominant_pass: int, alg_bytes: float):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary (profiles/traffic_x_pass.json: traffic / algorithmic bytes on a
-    smaller case), or None when that kernel's source has changed since."""
+    smaller case), or None when that kernel's source (its definition, its
+    launcher and the tensor-map builder) has changed since."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_x_pass.json")) as f:
             d = json.load(f)
-        with open(os.path.join(ROOT, d["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        with open(os.path.join(ROOT, d["source"])) as f:
+            src = kernel_source(f.read(), d["functions"])
+        sha = hashlib.sha256(src.encode()).hexdigest() if src else None
     except Exception:
         return None
-    if dominant_pass != 0 or sha != d.get("source_sha256"):
+    if dominant_pass != 0 or sha is None or sha != d.get("functions_sha256"):
         return None
     return d["traffic_over_algorithmic"] * alg_bytes
 

@@ -238,6 +238,9 @@ def surrogate_bench(args):
     seeds = range(1000, 1000 + NB)
     c0 = torch.stack([torch.from_numpy(inputs.uniform_field(shape, seed=s, offset=inputs.trajectory_mean(s)))
                       for s in seeds]).cuda()
+    # the guard's one torch reduction: its first call in a process carries a one-time
+    # cost of the installed torch build (about 2 s here), kept out of the timed region
+    float(c0[0].abs().double().sum())
     # plain solver: 8 fields x 30 steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()

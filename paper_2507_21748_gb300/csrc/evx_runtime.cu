@@ -476,9 +476,10 @@ evx_status evx_set_field_host(evx_grid* g, const float* h_c) {
         g->has_field = true;
         return EVX_OK;
     }
-    evx_status s = host_rows_copy(g, const_cast<float*>(h_c), true);
-    if (s != EVX_OK) return s;
-    s = load_real(g, (const float*)g->W, 2LL * g->Zp, 0);
+    // one contiguous copy into S's memory (the state is rebuilt from it: the R2C
+    // reads it before the x pass overwrites S), then the caller-order row map
+    CK(cudaMemcpyAsync(g->S, h_c, field_bytes(g), cudaMemcpyHostToDevice, g->st));
+    evx_status s = load_real(g, reinterpret_cast<const float*>(g->S), g->nz, 1);
     if (s != EVX_OK) return s;
     CK(cudaStreamSynchronize(g->st));
     return EVX_OK;

@@ -78,3 +78,25 @@ def test_null_arguments(lib):
     lib.evx_energy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.evx_energy(None, None, None) == 1
     assert lib.evx_grid_destroy(None) == 0
+
+
+def test_model_and_engine_entry_points_reject_bad_arguments(lib):
+    """Host-side argument checks of the model and engine calls (no device work)."""
+    lib.evx_set_model.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.evx_get_model.argtypes = [ctypes.c_void_p]
+    lib.evx_get_model.restype = ctypes.c_int
+    lib.evx_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.evx_set_model(None, 1) == 1   # EVX_ERR_ARG
+    assert lib.evx_get_model(None) == -1
+    assert lib.evx_step(None, 1) == 1
+    lib.evx_nn_set_conv_engine.argtypes = [ctypes.c_int]
+    lib.evx_nn_conv_engine.restype = ctypes.c_int
+    assert lib.evx_nn_set_conv_engine(7) == 1
+    assert lib.evx_nn_set_conv_engine(1) == 0 and lib.evx_nn_conv_engine() == 1
+    assert lib.evx_nn_set_conv_engine(0) == 0 and lib.evx_nn_conv_engine() == 0
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    lib.evx_nn_conv3d.argtypes = [vp] * 6 + [i] * 7 + [vp]
+    assert lib.evx_nn_conv3d(None, None, None, None, None, None, 1, 1, 2, 64, 32, 32, 0, None) == 1
+    one = ctypes.c_void_p(16)  # never dereferenced: the size check comes first
+    assert lib.evx_nn_conv3d(one, one, None, one, None, None, 1, 1, 3, 64, 32, 32, 0, None) == 2  # Y odd
+    assert lib.evx_nn_conv3d(one, one, None, one, None, None, 1, 1, 2, 48, 32, 32, 0, None) == 2  # Z % 64

@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--train-iters", type=int, default=200)
+    ap.add_argument("--train-iters", type=int, default=500)
     ap.add_argument("--ac-steps", type=int, default=50, help="Allen-Cahn steps timed after the CH run (0: skip)")
     ap.add_argument("--vm-steps", type=int, default=20,
                     help="variable-mobility CH steps timed after the CH run (0: skip)")
@@ -224,7 +224,7 @@ def surrogate_bench(args):
     net = S.Net(tr_shape, B, seed=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = S.train(net, pool, args.train_iters, lr=2e-3, lr_final=2e-4)
+    hist = S.train(net, pool, args.train_iters, lr=1.5e-3, lr_final=4e-4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     out["train"] = {"grid": "128^3", "batch": B, "iters": args.train_iters, "pairs": B * args.train_iters,

@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int n
 // accelerator: one thread issues cp.async.bulk.tensor boxes of up to 256 rows
 // of 8 complex values (64 bytes); loads complete on an mbarrier, stores are
 // bulk groups read out of a shared-memory staging tile. Every wait is bounded:
-// on timeout the kernel records it in g_timeout and leaves its tile loop.
+// on timeout the kernel records it in g_timeout (mbar_wait_or_abort).
 __device__ int g_timeout;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -496,6 +496,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "memory");
         if (ok) return true;
         if (clock64() - t0 > (1LL << 32)) return false;
+    }
+}
+
+// bounded wait that gives up at once when another thread of the CTA already has:
+// the first thread to run out of time sets *abort_flag and g_timeout. Callers do
+// not leave their tile loop on failure (every thread keeps the same barrier
+// sequence, so no vote is needed); the remaining tiles are processed from stale
+// buffers without waiting and the host reports the flag.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > (1LL << 32)) {
+            *abort_flag = 1;
+            atomicExch(&g_timeout, 1);
+            return false;
+        }
     }
 }
 // 4D tensor {kz, y within block, x, y block} of a y-blocked half spectrum
@@ -539,7 +565,11 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
     fill_twiddles<TP>(tA, tB, a.tw, 8 * TP);
-    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        s_abort = 0;
+    }
     __syncthreads();
     auto issue = [&](int tl) {
         const int outer = tl / nchunks, chunk = tl - outer * nchunks;
@@ -551,11 +581,7 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
     if (threadIdx.x == 0) issue(tile);
     uint32_t parity = 0;
     for (; tile < ntiles; tile += gridDim.x) {
-        const bool ok = mbar_wait(bar, parity);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
-            break;
-        }
+        mbar_wait_or_abort(bar, parity, &s_abort);
         parity ^= 1;
         float2 v[32];
 #pragma unroll
@@ -609,9 +635,11 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
     if (tile >= ntiles) return;
     fill_twiddles<TP>(tA, tB, a.tw, 8 * TP);
     for (int i = threadIdx.x; i < L; i += 8 * TP) k2xs[i] = a.k2x[i];
+    __shared__ int s_abort;
     if (threadIdx.x == 0) {
         mbar_init(bars + 0, 1);
         mbar_init(bars + 1, 1);
+        s_abort = 0;
     }
     __syncthreads();
     const int YB = a.YB;
@@ -634,11 +662,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         const int ky = tile / nchunks, chunk = tile - ky * nchunks;
         const int next = tile + gridDim.x;
         // ---- g_hat = F_x W, kept as G = -dt M |k|^2 g_hat (Allen-Cahn: -dt L g_hat)
-        bool ok = mbar_wait(bars + 0, parity);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
-            break;
-        }
+        mbar_wait_or_abort(bars + 0, parity, &s_abort);
         float2 v[32];
 #pragma unroll
         for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufW[(n2 + TP * n1) * 8 + p];
@@ -669,11 +693,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
             for (int q = 0; q < 32; ++q) v[q] = G[q];
         } else {
             // ---- c_hat = F_x S
-            ok = mbar_wait(bars + 1, parity);
-            if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
-                break;
-            }
+            mbar_wait_or_abort(bars + 1, parity, &s_abort);
             parity ^= 1;
 #pragma unroll
             for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufS[(n2 + TP * n1) * 8 + p];

@@ -50,6 +50,22 @@ evx_status evx_nn_conv3d(const void *in, const void *w, const float *bias, void 
                          const void *res, int B, int X, int Y, int Z, int cin, int cout, int epilogue,
                          void *stream);
 
+/* The network's lift and projection as direct sums (CUDA cores): a convolution
+ * whose input (lift) or output (projection) is a single field would spend
+ * 15/16 of a 16-channel tensor-core GEMM on zero padding.
+ * evx_nn_lift: out(v, co) = bias(co) + sum_t w[t][co][0] BF16(scale f(v + off_t))
+ *   for co < cout = 32; w is the [27][cout][cin] weight of the padded lift
+ *   (only input channel 0 used); f FP32 field, out BF16 [..][32]. Equals
+ *   evx_nn_field_to_act + evx_nn_conv3d(EPI_PLAIN) up to FP32 summation order.
+ * evx_nn_project: out(v) = bias(0) + sum_t sum_ci w[t][0][ci] h(v + off_t, ci)
+ *   with cin = 32; w [27][cout][32] (output channel 0 used); h BF16, out FP32
+ *   field. Equals evx_nn_conv3d(EPI_FIELD) up to summation order.
+ * Any B, X, Y, Z >= 1 (periodic). */
+evx_status evx_nn_lift(const float *f, float scale, const void *w, int cin, int cout, const float *bias, void *out,
+                       int B, int X, int Y, int Z, void *stream);
+evx_status evx_nn_project(const void *h, const void *w, int cin, int cout, const float *bias, float *out, int B,
+                          int X, int Y, int Z, void *stream);
+
 /* Weight gradient of out = conv(x, W): dw[t][co][ci] = sum_v dy(v, co) x(v + off_t, ci)
  * (FP32). partials: device scratch of partial_floats floats (at least
  * 27 * cin * cout; more allows more CTAs), reduced in a fixed order. */

@@ -16,6 +16,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "evx_internal.h"
 
@@ -759,6 +760,8 @@ template <typename K>
 static cudaError_t prep(K kernel, size_t smem, int threads, int* grid_per_sm) {
     static PrepEntry cache[64];
     static int ncache = 0;
+    static std::mutex mu;  // grids may be driven from several host threads
+    std::lock_guard<std::mutex> lock(mu);
     const void* key = (const void*)kernel;
     int dev = 0;
     cudaGetDevice(&dev);

@@ -350,6 +350,119 @@ __global__ void f32_to_bf16_kernel(const float* a, int n, __nv_bfloat16* b) {
         b[i] = __float2bfloat16_rn(a[i]);
 }
 
+// ------------------------------------------- direct lift and projection
+// The network's first and last convolutions touch one field: the lift reads
+// only channel 0 of its (zero-padded) input, the projection writes only
+// channel 0. As tensor-core GEMMs they would spend 15/16 of the work on
+// zeros; here they are direct 3x3x3 sums on the CUDA cores, one voxel per
+// thread (864 FMAs), weights broadcast from shared memory, neighbour loads
+// coalesced along z (a warp covers 32 consecutive voxels of a row).
+__device__ __forceinline__ void vox_coords(long long v, int X, int Y, int Z, int& b, int& x, int& y, int& z) {
+    z = (int)(v % Z);
+    long long r = v / Z;
+    y = (int)(r % Y);
+    r /= Y;
+    x = (int)(r % X);
+    b = (int)(r / X);
+}
+
+// out(v, co) = bias(co) + sum_t w[t][co][0] BF16(scale f(v + off_t)), co < 32
+__global__ void __launch_bounds__(256) lift_direct_kernel(const float* __restrict__ f, float scale,
+                                                           const __nv_bfloat16* __restrict__ w, int wcin,
+                                                           const float* __restrict__ bias, __nv_bfloat16* out, int B,
+                                                           int X, int Y, int Z) {
+    __shared__ float4 ws[27][8];  // w[t][co][0], co = 4 q .. 4 q + 3
+    __shared__ float bs[32];
+    for (int i = threadIdx.x; i < 27 * 32; i += blockDim.x) {
+        const int t = i >> 5, co = i & 31;
+        reinterpret_cast<float*>(&ws[t][0])[co] = __bfloat162float(w[(t * 32 + co) * wcin]);
+    }
+    if (threadIdx.x < 32) bs[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
+    __syncthreads();
+    const long long nvox = (long long)B * X * Y * Z;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        int b, x, y, z;
+        vox_coords(v, X, Y, Z, b, x, y, z);
+        float acc[32];
+#pragma unroll
+        for (int co = 0; co < 32; ++co) acc[co] = bs[co];
+#pragma unroll 1
+        for (int t = 0; t < 27; ++t) {
+            const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
+            const int xx = x + dx < 0 ? X - 1 : (x + dx == X ? 0 : x + dx);
+            const int yy = y + dy < 0 ? Y - 1 : (y + dy == Y ? 0 : y + dy);
+            const int zz = z + dz < 0 ? Z - 1 : (z + dz == Z ? 0 : z + dz);
+            const float val =
+                __bfloat162float(__float2bfloat16_rn(scale * f[(((long long)b * X + xx) * Y + yy) * Z + zz]));
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 wq = ws[t][q];
+                acc[4 * q] = fmaf(wq.x, val, acc[4 * q]);
+                acc[4 * q + 1] = fmaf(wq.y, val, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(wq.z, val, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(wq.w, val, acc[4 * q + 3]);
+            }
+        }
+        uint4* o = reinterpret_cast<uint4*>(out + v * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 pk;
+            __nv_bfloat162* pp = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pp[j] = __floats2bfloat162_rn(acc[8 * q + 2 * j], acc[8 * q + 2 * j + 1]);
+            o[q] = pk;
+        }
+    }
+}
+
+// out(v) = bias(0) + sum_t sum_ci w[t][0][ci] h(v + off_t, ci), ci < 32, FP32 field;
+// w is [27][wcout][32] (row 0 of each tap used)
+__global__ void __launch_bounds__(256) project_direct_kernel(const __nv_bfloat16* __restrict__ h,
+                                                              const __nv_bfloat16* __restrict__ w, int wcout,
+                                                              const float* __restrict__ bias, float* out, int B,
+                                                              int X, int Y, int Z) {
+    __shared__ float4 ws[27][8];  // w[t][0][ci], ci = 4 q .. 4 q + 3
+    for (int i = threadIdx.x; i < 27 * 32; i += blockDim.x) {
+        const int t = i >> 5, ci = i & 31;
+        reinterpret_cast<float*>(&ws[t][0])[ci] = __bfloat162float(w[(long long)t * wcout * 32 + ci]);
+    }
+    __syncthreads();
+    const float b0 = bias ? bias[0] : 0.f;
+    const long long nvox = (long long)B * X * Y * Z;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long long)gridDim.x * blockDim.x) {
+        int b, x, y, z;
+        vox_coords(v, X, Y, Z, b, x, y, z);
+        float acc = b0;
+#pragma unroll 1
+        for (int t = 0; t < 27; ++t) {
+            const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
+            const int xx = x + dx < 0 ? X - 1 : (x + dx == X ? 0 : x + dx);
+            const int yy = y + dy < 0 ? Y - 1 : (y + dy == Y ? 0 : y + dy);
+            const int zz = z + dz < 0 ? Z - 1 : (z + dz == Z ? 0 : z + dz);
+            const uint4* hp = reinterpret_cast<const uint4*>(h + ((((long long)b * X + xx) * Y + yy) * Z + zz) * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 hv = hp[q];
+                const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&hv);
+                const float4 wa = ws[t][2 * q], wb = ws[t][2 * q + 1];
+                const float2 h0 = __bfloat1622float2(h2[0]), h1 = __bfloat1622float2(h2[1]);
+                const float2 h2f = __bfloat1622float2(h2[2]), h3 = __bfloat1622float2(h2[3]);
+                acc = fmaf(wa.x, h0.x, acc);
+                acc = fmaf(wa.y, h0.y, acc);
+                acc = fmaf(wa.z, h1.x, acc);
+                acc = fmaf(wa.w, h1.y, acc);
+                acc = fmaf(wb.x, h2f.x, acc);
+                acc = fmaf(wb.y, h2f.y, acc);
+                acc = fmaf(wb.z, h3.x, acc);
+                acc = fmaf(wb.w, h3.y, acc);
+            }
+        }
+        out[v] = acc;
+    }
+}
+
 }  // namespace evxnn
 
 // ===================================================================== C-ABI
@@ -480,6 +593,26 @@ evx_status evx_nn_conv3d(const void* in, const void* w, const float* bias, void*
     if (cin == 32 && cout == 16) return conv_epi<32, 16>(epilogue, a, st);
     if (cin == 16 && cout == 16) return conv_epi<16, 16>(epilogue, a, st);
     return nn_fail(EVX_ERR_ARG, "supported channel pairs: 16/32 -> 16/32");
+}
+
+evx_status evx_nn_lift(const float* f, float scale, const void* w, int cin, int cout, const float* bias, void* out,
+                       int B, int X, int Y, int Z, void* stream) {
+    if (!f || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
+    if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
+    if (cout != 32 || cin < 1) return nn_fail(EVX_ERR_ARG, "lift: cout must be 32, cin >= 1");
+    lift_direct_kernel<<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+        f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, B, X, Y, Z);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_project(const void* h, const void* w, int cin, int cout, const float* bias, float* out, int B,
+                          int X, int Y, int Z, void* stream) {
+    if (!h || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
+    if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
+    if (cin != 32 || cout < 1) return nn_fail(EVX_ERR_ARG, "project: cin must be 32, cout >= 1");
+    project_direct_kernel<<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)h, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
+    return nn_cuda(cudaGetLastError());
 }
 
 evx_status evx_nn_conv3d_wgrad(const void* dy, const void* x, float* dw, float* partials, size_t partial_floats,

@@ -18,6 +18,7 @@ lib = evx.lib
 NN_EXPORTS = ["evx_nn_conv3d", "evx_nn_conv3d_wgrad", "evx_nn_bias_grad", "evx_nn_flip_weights",
               "evx_nn_field_to_act", "evx_nn_zero_mean_add", "evx_nn_mse", "evx_nn_adam",
               "evx_nn_f32_to_bf16", "evx_nn_set_conv_engine", "evx_nn_conv_engine", "evx_nn_check",
+              "evx_nn_lift", "evx_nn_project",
               "evx_nn_last_error"]
 EPI_PLAIN, EPI_GELU, EPI_RESID, EPI_GELU_BWD, EPI_FIELD = range(5)
 ENGINE_TCGEN05, ENGINE_MMA_SYNC = 0, 1
@@ -36,6 +37,8 @@ def _setup():
         "evx_nn_adam": [vp, vp, vp, vp, i, f, f, f, f, i, vp, vp],
         "evx_nn_f32_to_bf16": [vp, i, vp, vp],
         "evx_nn_set_conv_engine": [i],
+        "evx_nn_lift": [vp, f, vp, i, i, vp, vp, i, i, i, i, vp],
+        "evx_nn_project": [vp, vp, i, i, vp, vp, i, i, i, i, vp],
         "evx_nn_conv_engine": [],
         "evx_nn_check": [],
     }
@@ -122,7 +125,8 @@ class Net:
         self._refresh_bf16()
         bf = torch.bfloat16
         nv = self.nvox
-        self.a_in = torch.empty((nv, self.CIN), dtype=bf, device=dev)
+        # the padded lift input: for the lift's weight gradient, or for the tensor-core lift when W != 32
+        self.a_in = torch.empty((nv, self.CIN), dtype=bf, device=dev) if (train or W != 32) else None
         if not train:
             # inference: the residual stream is updated in place; one GELU input/output pair
             h, u, a = (torch.empty((nv, W), dtype=bf, device=dev) for _ in range(3))
@@ -199,13 +203,25 @@ class Net:
         self._c = c
         s = _stream()
         W = self.W
-        _ck(lib.evx_nn_field_to_act(_p(c), self.nvox, self.CIN, 1.0, _p(self.a_in), s))
-        self._conv(self.a_in, "W0", self.p["b0"], self.h[0], self.CIN, W, EPI_PLAIN)
+        X, Y, Z = self.shape
+        if self.training:  # the padded input is kept for the lift's weight gradient
+            _ck(lib.evx_nn_field_to_act(_p(c), self.nvox, self.CIN, 1.0, _p(self.a_in), s))
+        if W == 32:  # direct sum: only input channel 0 is nonzero
+            _ck(lib.evx_nn_lift(_p(c), 1.0, _p(self.wbf["W0"]), self.CIN, W, _p(self.p["b0"]), _p(self.h[0]),
+                                self.batch, X, Y, Z, s))
+        else:
+            if not self.training:
+                _ck(lib.evx_nn_field_to_act(_p(c), self.nvox, self.CIN, 1.0, _p(self.a_in), s))
+            self._conv(self.a_in, "W0", self.p["b0"], self.h[0], self.CIN, W, EPI_PLAIN)
         for k in range(self.nb):
             self._conv(self.h[k], "W1_%d" % k, self.p["b1_%d" % k], self.a[k], W, W, EPI_GELU, pre=self.u[k])
             self._conv(self.a[k], "W2_%d" % k, self.p["b2_%d" % k], self.h[k + 1], W, W, EPI_RESID,
                        res=self.h[k])
-        self._conv(self.h[self.nb], "Wp", self.p["bp"], self.d, W, self.CPROJ, EPI_FIELD)
+        if W == 32:  # direct sum: only output channel 0 is used
+            _ck(lib.evx_nn_project(_p(self.h[self.nb]), _p(self.wbf["Wp"]), W, self.CPROJ, _p(self.p["bp"]),
+                                   _p(self.d), self.batch, X, Y, Z, s))
+        else:
+            self._conv(self.h[self.nb], "Wp", self.p["bp"], self.d, W, self.CPROJ, EPI_FIELD)
         _ck(lib.evx_nn_zero_mean_add(_p(c), _p(self.d), self.batch, self.V, _p(self.dpart), self.nparts,
                                      _p(self.pred), s))
         return self.pred.view(c.shape)

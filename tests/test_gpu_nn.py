@@ -127,6 +127,50 @@ def test_conv_engine_setting(S):
     S.check()
 
 
+@pytest.mark.parametrize("shape", [(2, 4, 6, 64), (1, 3, 5, 7), (1, 1, 1, 9)])
+def test_direct_lift_and_projection(S, shape):
+    """evx_nn_lift and evx_nn_project against the FP64 oracle's conv on the padded
+    input / channel 0 of the output, and against the tensor-core convolutions
+    they replace (same BF16 operands: FP32 sums in another order); any sizes,
+    periodic (X = Y = 1 wraps every neighbour onto the voxel's own row)."""
+    import torch
+    rng = np.random.default_rng(sum(shape))
+    B, X, Y, Z = shape
+    f = rng.standard_normal(shape).astype(np.float32)
+    w0 = rng.standard_normal((27, 32, 16)) * 0.2
+    w0[:, :, 1:] = 0.0
+    w0 = bf16(w0)
+    b0 = torch.from_numpy(rng.standard_normal(32).astype(np.float32))
+    fd, w0d, b0d = torch.from_numpy(f).cuda(), w0.cuda(), b0.cuda()
+    h = torch.empty(shape + (32,), dtype=torch.bfloat16, device="cuda")
+    S._ck(S.lib.evx_nn_lift(S._p(fd), 1.0, S._p(w0d), 16, 32, S._p(b0d), S._p(h), B, X, Y, Z, S._stream()))
+    wp = bf16(rng.standard_normal((27, 16, 32)) * 0.1)
+    bp = torch.from_numpy(rng.standard_normal(16).astype(np.float32))
+    hin = bf16(rng.standard_normal(shape + (32,)))
+    hd, wpd, bpd = hin.cuda(), wp.cuda(), bp.cuda()
+    d = torch.empty(shape, dtype=torch.float32, device="cuda")
+    S._ck(S.lib.evx_nn_project(S._p(hd), S._p(wpd), 32, 16, S._p(bpd), S._p(d), B, X, Y, Z, S._stream()))
+    torch.cuda.synchronize()
+    a_in = N.field_to_act(bf16(f).float().numpy().astype(np.float64))
+    ref_h = N.conv(a_in, w0.float().numpy().astype(np.float64), b0.numpy().astype(np.float64))
+    assert rel(h.float().cpu().numpy(), ref_h) < 8e-3  # BF16 output rounding
+    ref_d = N.conv(hin.float().numpy().astype(np.float64), wp.float().numpy().astype(np.float64),
+                   bp.numpy().astype(np.float64))[..., 0]
+    assert rel(d.cpu().numpy(), ref_d) < 1e-5  # FP32 output
+    if Z % 64 == 0 and Y % 2 == 0:  # the tensor-core path these replace
+        act = torch.empty(shape + (16,), dtype=torch.bfloat16, device="cuda")
+        S._ck(S.lib.evx_nn_field_to_act(S._p(fd), B * X * Y * Z, 16, 1.0, S._p(act), S._stream()))
+        h2 = torch.empty_like(h)
+        S._ck(S.lib.evx_nn_conv3d(S._p(act), S._p(w0d), S._p(b0d), S._p(h2), None, None, B, X, Y, Z, 16, 32, 0,
+                                  S._stream()))
+        d2 = torch.empty_like(d)
+        S._ck(S.lib.evx_nn_conv3d(S._p(hd), S._p(wpd), S._p(bpd), S._p(d2), None, None, B, X, Y, Z, 32, 16, 4,
+                                  S._stream()))
+        torch.cuda.synchronize()
+        assert rel(h.float().cpu().numpy(), h2.float().cpu().numpy()) < 8e-3
+        assert rel(d.cpu().numpy(), d2.cpu().numpy()) < 1e-5
+
+
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16)])
 def test_conv_dgrad_and_wgrad(S, cin, cout):
     import torch

@@ -213,7 +213,7 @@ def surrogate_bench(args):
     """Learned surrogate (10 solver steps per block): train at 128^3 on solver
     trajectories (seeds 0..255, mean in [-0.3, 0.3], noise 0.05), then advance 8
     fields of 256^3 by 3 blocks with the guarded surrogate and with the plain
-    solver; report times, the surrogate's error judged by the solver and the
+    solver; report times, the surrogate's error against the solver and the
     conv kernel's tensor throughput."""
     import torch
     from paper_2507_21748_gb300 import evx, inputs

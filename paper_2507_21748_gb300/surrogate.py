@@ -1,10 +1,10 @@
-"""Learned surrogate of the semi-implicit Cahn-Hilliard step (binding + driver).
+"""Learned surrogate of the semi-implicit Cahn-Hilliard step (binding, training and guarded rollout).
 
 A 3D residual CNN advances the field by a block of solver steps (C-ABI in
 include/evx_nn.h). Every forward, backward and optimiser step runs in
 libevx's kernels; PyTorch only provides device buffers. The plain solver
 generates the training pairs, serves as fallback when the surrogate's mass
-drift or energy increase exceeds a threshold, and judges its error.
+drift or energy increase exceeds a threshold, and measures its error against the solver.
 """
 import ctypes
 import time
@@ -330,11 +330,11 @@ def rollout(net, c0, nblocks, block=10, dt=0.1, M=1.0, kappa=1.0, mass_tol=1e-6,
     recomputed by the plain solver for that block. Returns (fields, stats)."""
     shape = tuple(c0.shape[1:])
     B = c0.shape[0]
-    judge = evx.Grid(shape, dt=dt, M=M, kappa=kappa)
+    referee = evx.Grid(shape, dt=dt, M=M, kappa=kappa)
     c = c0.clone()
     fallbacks = 0
     t_net = t_guard = t_fb = 0.0
-    E_prev = [None] * B  # judged energy and mass of each sample's current field
+    E_prev = [None] * B  # refereed energy and mass of each sample's current field
     for _ in range(nblocks):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -344,26 +344,26 @@ def rollout(net, c0, nblocks, block=10, dt=0.1, M=1.0, kappa=1.0, mass_tol=1e-6,
         t_net += t1 - t0
         for i in range(B):
             if E_prev[i] is None:
-                judge.set_field(c[i])
-                E_prev[i] = judge.energy()
+                referee.set_field(c[i])
+                E_prev[i] = referee.energy()
             E0, m0 = E_prev[i]
             l1 = float(c[i].abs().double().sum())
-            judge.set_field(pred[i])
-            E1, m1 = judge.energy()
+            referee.set_field(pred[i])
+            E1, m1 = referee.energy()
             ok = abs(m1 - m0) <= mass_tol * l1 and E1 <= E0 * (1 + energy_tol) + 1e-300
             E_prev[i] = (E1, m1)
             t2 = time.perf_counter()
             if not ok:
-                judge.set_field(c[i])
-                judge.step(block)
-                judge.get_field(pred[i])
-                E_prev[i] = None  # judged afresh next block
+                referee.set_field(c[i])
+                referee.step(block)
+                referee.get_field(pred[i])
+                E_prev[i] = None  # checked afresh next block
                 fallbacks += 1
                 torch.cuda.synchronize()
                 t_fb += time.perf_counter() - t2
         t_guard += time.perf_counter() - t1
         c = pred
-    judge.close()
+    referee.close()
     return c, {"fallbacks": fallbacks, "blocks": nblocks * B, "t_net_s": t_net, "t_guard_s": t_guard - t_fb,
                "t_fallback_s": t_fb}
 

@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the 64^3 / 256^3 / 400^3 timings")
     ap.add_argument("--train-iters", type=int, default=500)
     ap.add_argument("--ac-steps", type=int, default=50, help="Allen-Cahn steps timed after the CH run (0: skip)")
     ap.add_argument("--vm-steps", type=int, default=20,
@@ -301,6 +302,33 @@ def surrogate_bench(args):
     return out
 
 
+def small_grid_bench():
+    """The smaller configurations: 64^3 (100-step runs; L2-resident, so latency,
+    not bandwidth) and 256^3 / 400^3 (1000-step runs) with the same recipe as the
+    parity tests (c0 = U(-0.05, 0.05), seed 0); CUDA-graph launches, CUDA events."""
+    import torch
+    from paper_2507_21748_gb300 import evx, inputs
+    out = {}
+    for n, steps in ((64, 1000), (256, 1000), (400, 200)):
+        shape = (n, n, n)
+        g = evx.Grid(shape, dt=DT, M=MOB, kappa=KAPPA, h=H)
+        g.set_field(torch.from_numpy(inputs.uniform_field(shape, seed=0)).cuda())
+        g.step(20)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["%d^3" % n] = {"steps": steps, "us_per_step": 1e3 * ms / steps,
+                           "voxel_steps_per_s": steps * float(n) ** 3 / (ms * 1e-3),
+                           "footprint_bytes": g.footprint(),
+                           "kernels": "fast" if n in (64, 128, 256, 512, 1024) else "generic (400 = 5*5*16)"}
+        g.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
@@ -516,6 +544,12 @@ def main():
         except Exception as ex:  # report, do not fail the bench
             sur = {"error": repr(ex)}
 
+    small = None
+    if not args.no_small and args.n == 1024:
+        try:
+            small = small_grid_bench()
+        except Exception as ex:  # report, do not fail the bench
+            small = {"error": repr(ex)}
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -552,6 +586,7 @@ def main():
         "gpu_launches": 4 * args.steps,
         "allen_cahn": ac,
         "variable_mobility": vm,
+        "small_grids": small,
         "surrogate": sur,
     }
     print(json.dumps(out), flush=True)

@@ -225,8 +225,22 @@ struct RingArgs {
     int nunits;  // B * X * nzc * nseg
 };
 
-// bounded wait that also gives up once another role has aborted
+// non-blocking probe of a phase (no suspend, unlike try_wait)
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait that also gives up once another role has aborted; a phase that has
+// already completed is seen by the non-blocking probe first
 __device__ __forceinline__ bool ring_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try(bar, parity)) return true;

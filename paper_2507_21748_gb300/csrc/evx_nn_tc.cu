@@ -25,10 +25,11 @@
 // accumulate; an output row is complete after its third input row.
 //   warp 0      producer: per slot 9 TMA loads (per dx the 128 rows z0 ..
 //               and two 16-row halo boxes at (z0-16) mod Z, (z0+128) mod Z);
-//               full/empty mbarriers per slot
+//               a full mbarrier per slot; a slot is refilled once the
+//               commit of the row it held (below) has fired
 //   warp 1      MMA issuer: the warp walks the schedule, lane 0 waits, issues
-//               and commits (slot freed after its 18 MMAs; a block's barrier
-//               once its output row is complete)
+//               and commits once per input row, on the block of the output row
+//               that row completes (which also frees the row's slot)
 //   warps 2..9  epilogue: each warp reads 16 columns of its 32 lanes of a
 //               completed block (tcgen05.ld), zeroes them (tcgen05.st), frees
 //               the block, applies bias and the fused epilogue and stores BF16
@@ -212,8 +213,8 @@ constexpr int WB = 9 * 12 * 4 * 128;       // staged weights: [dx][dz][n/8 (12)]
 constexpr int NBLK = 16;                   // accumulator blocks of 32 columns (a ring over output rows)
 constexpr int NEPI = 8;                    // epilogue warps
 constexpr int NTH = (2 + NEPI) * 32;
-constexpr int BAR = WB + NS * SLOT;        // barriers: full[NS], empty[NS], tfull[NBLK], tempty[NBLK]
-constexpr int SMEM = BAR + 8 * (2 * NS + 2 * NBLK) + 16 + 1024;  // + tensor-memory slot, abort flag, alignment
+constexpr int BAR = WB + NS * SLOT;        // barriers: full[NS], tfull[NBLK], tempty[NBLK]
+constexpr int SMEM = BAR + 8 * (NS + 2 * NBLK) + 16 + 1024;  // + tensor-memory slot, abort flag, alignment
 constexpr uint32_t SLOT_TX = SLOT;         // TMA bytes per slot
 constexpr long long WAIT_BUDGET = 1LL << 31;
 }  // namespace ring
@@ -291,9 +292,8 @@ __global__ void __launch_bounds__(ring::NTH, 1)
     unsigned char* sm = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);  // swizzle atoms: 1024-aligned
     unsigned char* swb = sm;
     unsigned char* sring = sm + WB;
-    const uint32_t full = smem_addr(sm + BAR), empty = full + 8 * NS, tfull = empty + 8 * NS,
-                   tempty = tfull + 8 * NBLK;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + BAR + 8 * (2 * NS + 2 * NBLK));
+    const uint32_t full = smem_addr(sm + BAR), tfull = full + 8 * NS, tempty = tfull + 8 * NBLK;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + BAR + 8 * (NS + 2 * NBLK));
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const ConvArgs& a = r.a;
@@ -314,10 +314,7 @@ __global__ void __launch_bounds__(ring::NTH, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) {
-            mbar_init(full + 8 * s, 1);
-            mbar_init(empty + 8 * s, 1);
-        }
+        for (int s = 0; s < NS; ++s) mbar_init(full + 8 * s, 1);
         for (int c = 0; c < NBLK; ++c) {
             mbar_init(tfull + 8 * c, 1);
             mbar_init(tempty + 8 * c, NEPI);
@@ -341,7 +338,11 @@ __global__ void __launch_bounds__(ring::NTH, 1)
 
     if (warp == 0) {
         // ---------------------------------------------------------- producer
-        uint32_t k = 0;  // slots issued
+        // A slot is refilled once the MMAs of the row it last held have completed:
+        // the MMA warp's commit on that row's accumulator block (virtual row
+        // vslot[slot]) already signals it, so the slot needs no barrier of its own.
+        uint32_t k = 0, V = 0;  // slots issued; first virtual row of the unit
+        uint32_t vslot[NS];
         bool ok = true;
         for (int u = blockIdx.x; u < r.nunits && ok; u += gridDim.x) {
             int bx, z0, ys, ye;
@@ -351,7 +352,9 @@ __global__ void __launch_bounds__(ring::NTH, 1)
                 const int yp = (ys + j + Y) % Y;
                 const uint32_t slot = k % NS;
                 uint32_t w_ok = 1;
-                if (lane == 0 && k >= NS) w_ok = ring_wait(empty + 8 * slot, ((k / NS) & 1) ^ 1, abort_flag);
+                if (lane == 0 && k >= NS)
+                    w_ok = ring_wait(tfull + 8 * ring_blk(vslot[slot]), (vslot[slot] / NBLK) & 1, abort_flag);
+                vslot[slot] = V + (uint32_t)(j + 1);
                 if (!__shfl_sync(0xffffffffu, w_ok, 0)) {
                     ok = false;
                     break;
@@ -372,6 +375,7 @@ __global__ void __launch_bounds__(ring::NTH, 1)
                 __syncwarp();
                 ++k;
             }
+            V += (uint32_t)(ye - ys) + 4;
         }
         if (!ok && lane == 0)  // let this CTA's copies in flight land before it exits (bounded)
             for (uint32_t q = (k > (uint32_t)NS ? k - NS : 0); q < k; ++q) tc_wait(full + 8 * (q % NS), (q / NS) & 1);
@@ -395,12 +399,15 @@ __global__ void __launch_bounds__(ring::NTH, 1)
             for (uint32_t i = 0; i <= L + 1; ++i, ++k) {
                 // blocks are claimed 8 rows at a time (rows up to V+i+9, freed by the epilogue
                 // once it has read rows up to V+i-7), so the tensor-memory fence that orders
-                // the epilogue's reads before these MMAs runs once per 8 input rows
+                // the epilogue's reads before these MMAs runs once per 8 input rows. Every
+                // epilogue warp frees rows in order, so the phase of the last claimed block
+                // (row V+i-7 freed by all warps) implies the earlier ones: one probe, not 8,
+                // of a barrier the tensor core's operand reads make slow to reach.
                 const bool claim = V + i + 2 > vready;
                 uint32_t w_ok = 1;
                 if (lane == 0) {
-                    for (uint32_t v = vready + 1; claim && v <= V + i + 9 && w_ok; ++v)
-                        w_ok = ring_wait(tempty + 8 * ring_blk(v), ((v / NBLK) & 1) ^ 1, abort_flag);
+                    const uint32_t vc = V + i + 9;
+                    if (claim) w_ok = ring_wait(tempty + 8 * ring_blk(vc), ((vc / NBLK) & 1) ^ 1, abort_flag);
                     if (w_ok) w_ok = ring_wait(full + 8 * (k % NS), (k / NS) & 1, abort_flag);
                 }
                 if (!__shfl_sync(0xffffffffu, w_ok, 0)) {
@@ -436,8 +443,7 @@ __global__ void __launch_bounds__(ring::NTH, 1)
                     }
                 }
                 if (lane == 0) {
-                    tc_commit(empty + 8 * (k % NS));
-                    tc_commit(tfull + 8 * ring_blk(V + i));  // virtual row V+i has all its inputs
+                    tc_commit(tfull + 8 * ring_blk(V + i));  // virtual row V+i has all its inputs; slot k is free
                     if (i == L + 1) {
                         tc_commit(tfull + 8 * ring_blk(V + L + 2));
                         tc_commit(tfull + 8 * ring_blk(V + L + 3));

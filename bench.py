@@ -309,7 +309,7 @@ def small_grid_bench():
     import torch
     from paper_2507_21748_gb300 import evx, inputs
     out = {}
-    for n, steps in ((64, 1000), (256, 1000), (400, 200)):
+    for n, steps in ((64, 1000), (256, 1000), (400, 1000)):
         shape = (n, n, n)
         g = evx.Grid(shape, dt=DT, M=MOB, kappa=KAPPA, h=H)
         g.set_field(torch.from_numpy(inputs.uniform_field(shape, seed=0)).cuda())
@@ -324,7 +324,8 @@ def small_grid_bench():
         out["%d^3" % n] = {"steps": steps, "us_per_step": 1e3 * ms / steps,
                            "voxel_steps_per_s": steps * float(n) ** 3 / (ms * 1e-3),
                            "footprint_bytes": g.footprint(),
-                           "kernels": "fast" if n in (64, 128, 256, 512, 1024) else "generic (400 = 5*5*16)"}
+                           "kernels": "fast, L = 32 x TP" if n in (64, 128, 256, 512, 1024)
+                           else "fast, L = 20 x 20 (x, y), M = 200 = 20 x 10 (z)"}
         g.close()
     return out
 

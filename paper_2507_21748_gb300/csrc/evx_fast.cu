@@ -1,13 +1,14 @@
-// Fast paths of the four step passes for power-of-two lengths L = 32 * TP
-// (TP = 2 .. 32, i.e. L = 64 .. 1024; the z pass works on M = nz/2).
+// Fast paths of the four step passes for lengths L = R1 * TP: R1 = 32 with TP a
+// power of two 2 .. 32 (L = 64 .. 1024), and R1 = 20 with TP = 20 (L = 400) or
+// TP = 10 (the z pass of nz = 400, M = 200); the z pass works on M = nz/2.
 //
-// Four-step FFT of a length-L pencil, n = n2 + TP n1 (n2 < TP, n1 < 32):
-//   pass A:  Y[n2][k1] = sum_{n1} x[n2 + TP n1] w_32^{n1 k1}        (DFT-32 in registers)
+// Four-step FFT of a length-L pencil, n = n2 + TP n1 (n2 < TP, n1 < R1):
+//   pass A:  Y[n2][k1] = sum_{n1} x[n2 + TP n1] w_R1^{n1 k1}        (DFT-R1 in registers)
 //   twiddle: Y[n2][k1] *= w_L^{n2 k1}
-//   pass B:  X[k1 + 32 k2] = sum_{n2} Y[n2][k1] w_TP^{n2 k2}         (32/TP DFT-TP per thread)
-// Thread n2 of a pencil owns the 32 values x[n2 + TP n1] ("n2 ownership"); after
-// the one shared-memory transpose thread j owns X[k1 + 32 k2] for
-// k1 in [j 32/TP, (j+1) 32/TP), all k2 ("block ownership"). The inverse walks the
+//   pass B:  X[k1 + R1 k2] = sum_{n2} Y[n2][k1] w_TP^{n2 k2}         (R1/TP DFT-TP per thread)
+// Thread n2 of a pencil owns the R1 values x[n2 + TP n1] ("n2 ownership"); after
+// the one shared-memory transpose thread j owns X[k1 + R1 k2] for
+// k1 in [j R1/TP, (j+1) R1/TP), all k2 ("block ownership"). The inverse walks the
 // same way back. Global loads and stores go straight from/to registers in
 // both ownerships (each warp touches whole 64-byte row segments) for the z
 // pass, whose next tile is prefetched with cp.async; the x and y passes move
@@ -36,25 +37,25 @@ __device__ __forceinline__ void cp_wait() {
 
 // Twiddles of the four-step transform, re-indexed in shared memory so that
 // the threads of a warp read consecutive entries (no bank conflicts):
-//   tA[a * TP + n2]           = w_L^{n2 a}     (n2 ownership, a < 32)
+//   tA[a * TP + n2]           = w_L^{n2 a}     (n2 ownership, a < R1)
 //   tB[(c * NB + i) * TP + j] = w_L^{a c}, a = j NB + i  (block ownership)
 // both filled from the L-entry table tw[m] = w_L^m at kernel start.
-template <int TP>
+template <int R1, int TP>
 __device__ __forceinline__ void fill_twiddles(float2* tA, float2* tB, const float2* __restrict__ tw, int nthreads) {
-    constexpr int NB = 32 / TP, L = 32 * TP;
+    constexpr int NB = R1 / TP, L = R1 * TP;
     for (int idx = threadIdx.x; idx < L; idx += nthreads) {
         const int a = idx / TP, n2 = idx % TP;
         tA[idx] = tw[n2 * a];
-        const int c = idx / 32, rem = idx % 32, i = rem / TP, j = rem % TP;
+        const int c = idx / R1, rem = idx % R1, i = rem / TP, j = rem % TP;
         tB[idx] = tw[(j * NB + i) * c];
     }
 }
 
 // v[a] *= w_L^{+-n2 a}  (n2 ownership)
-template <int TP, int DIR>
-__device__ __forceinline__ void twiddle_a(float2 (&v)[32], int n2, const float2* tA) {
+template <int R1, int TP, int DIR>
+__device__ __forceinline__ void twiddle_a(float2 (&v)[R1], int n2, const float2* tA) {
 #pragma unroll
-    for (int a = 1; a < 32; ++a) {
+    for (int a = 1; a < R1; ++a) {
         float2 w = tA[a * TP + n2];
         if (DIR > 0) w.y = -w.y;
         v[a] = cmul(v[a], w);
@@ -62,9 +63,9 @@ __device__ __forceinline__ void twiddle_a(float2 (&v)[32], int n2, const float2*
 }
 
 // v[i TP + c] *= w_L^{+-a c}, a = j NB + i  (block ownership)
-template <int TP, int DIR>
-__device__ __forceinline__ void twiddle_b(float2 (&v)[32], int j, const float2* tB) {
-    constexpr int NB = 32 / TP;
+template <int R1, int TP, int DIR>
+__device__ __forceinline__ void twiddle_b(float2 (&v)[R1], int j, const float2* tB) {
+    constexpr int NB = R1 / TP;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
 #pragma unroll
@@ -76,45 +77,97 @@ __device__ __forceinline__ void twiddle_b(float2 (&v)[32], int j, const float2* 
     }
 }
 
-template <int TP, int DIR>
-__device__ __forceinline__ void pass_b(float2 (&v)[32]) {
+template <int R1, int TP, int DIR>
+__device__ __forceinline__ void pass_b(float2 (&v)[R1]) {
 #pragma unroll
-    for (int i = 0; i < 32 / TP; ++i) Dft<TP, DIR>::run(v + i * TP);
+    for (int i = 0; i < R1 / TP; ++i) Dft<TP, DIR>::run(v + i * TP);
 }
 
 // ---- shared-memory slots of the transposes
 // Column tiles (P pencils adjacent, p fastest): group G = a TP + n2 of P
-// complex, padded by one group per block a / (32/TP). Block-ownership
-// accesses of one warp then fall 33 groups apart (bank offsets 8 or 16
-// words) and n2-ownership accesses are contiguous: both conflict-free, and
-// every address is a per-thread base plus a compile-time offset.
-template <int TP, int P>
+// complex, padded by one group per block a / (R1/TP). For R1 = 32,
+// block-ownership accesses of one warp then fall 33 groups apart (bank
+// offsets 8 or 16 words) and n2-ownership accesses are contiguous: both
+// conflict-free, and every address is a per-thread base plus a compile-time
+// offset.
+template <int R1, int TP, int P>
 __device__ __forceinline__ int slot_s(int n2, int a, int p) {
-    constexpr int NB = 32 / TP;
+    constexpr int NB = R1 / TP;
     return (a * TP + n2 + a / NB) * P + p;
 }
-template <int TP, int P>
-__device__ __forceinline__ void t1_s(float2 (&v)[32], float2* xb, int n2, int p) {
-    constexpr int NB = 32 / TP;
+template <int R1, int TP, int P>
+__device__ __forceinline__ void t1_s(float2 (&v)[R1], float2* xb, int n2, int p) {
+    constexpr int NB = R1 / TP;
 #pragma unroll
-    for (int a = 0; a < 32; ++a) xb[slot_s<TP, P>(n2, a, p)] = v[a];
+    for (int a = 0; a < R1; ++a) xb[slot_s<R1, TP, P>(n2, a, p)] = v[a];
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
-        for (int c = 0; c < TP; ++c) v[i * TP + c] = xb[slot_s<TP, P>(c, n2 * NB + i, p)];
+        for (int c = 0; c < TP; ++c) v[i * TP + c] = xb[slot_s<R1, TP, P>(c, n2 * NB + i, p)];
 }
-template <int TP, int P>
-__device__ __forceinline__ void t2_s(float2 (&v)[32], float2* xb, int n2, int p) {
-    constexpr int NB = 32 / TP;
+template <int R1, int TP, int P>
+__device__ __forceinline__ void t2_s(float2 (&v)[R1], float2* xb, int n2, int p) {
+    constexpr int NB = R1 / TP;
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
-        for (int c = 0; c < TP; ++c) xb[slot_s<TP, P>(c, n2 * NB + i, p)] = v[i * TP + c];
+        for (int c = 0; c < TP; ++c) xb[slot_s<R1, TP, P>(c, n2 * NB + i, p)] = v[i * TP + c];
     __syncthreads();
 #pragma unroll
-    for (int a = 0; a < 32; ++a) v[a] = xb[slot_s<TP, P>(n2, a, p)];
+    for (int a = 0; a < R1; ++a) v[a] = xb[slot_s<R1, TP, P>(n2, a, p)];
 }
+
+// R2C post-processing of one row: thread n2 holds Z[n2 + TP d] (d < R1) of the
+// length-M complex transform Z of the packed real row; it writes, for its k,
+//   X_k = (Z_k + conj Z_{M-k})/2 - i e^{-2 pi i k/nz} (Z_k - conj Z_{M-k})/2
+// and thread 0 also X_M = Re Z_0 - Im Z_0. With R1 = 32 (TP a power of two
+// dividing 32) the partner Z[M - k] of k = n2 + TP d sits in thread TP - n2 of
+// the same warp at index 31 - d (thread 0: its own index 32 - d) and is
+// fetched by warp shuffle; otherwise the row passes through the M-entry shared
+// row xz. Every thread of the CTA calls this (it may synchronise the CTA).
+template <int R1, int TP>
+__device__ __forceinline__ void r2c_store(const float2 (&v)[R1], int n2, float2* xz, float2* out, bool rowok,
+                                          const float2* rtws) {
+    constexpr int M = R1 * TP;
+    if constexpr (R1 == 32) {
+        const int lane = threadIdx.x & 31;
+        const int src = (lane & ~(TP - 1)) | ((TP - n2) & (TP - 1));
+#pragma unroll
+        for (int d = 0; d < 32; ++d) {
+            float2 zm;
+            zm.x = __shfl_sync(0xffffffffu, v[31 - d].x, src);
+            zm.y = __shfl_sync(0xffffffffu, v[31 - d].y, src);
+            if (n2 == 0) zm = v[(32 - d) & 31];
+            const float2 zk = v[d];
+            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
+            const int k = n2 + TP * d;
+            if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < R1; ++d) xz[n2 + TP * d] = v[d];
+        __syncthreads();
+#pragma unroll
+        for (int d = 0; d < R1; ++d) {
+            const int k = n2 + TP * d;
+            const float2 zm = xz[k == 0 ? 0 : M - k];
+            const float2 zk = v[d];
+            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
+            if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
+        }
+    }
+    if (rowok && n2 == 0) out[M] = make_float2(v[0].x - v[0].y, 0.f);  // X_M = Re Z_0 - Im Z_0
+}
+
+// rows of the y-pass TMA box: up to 256 for R1 = 32 (y blocks of 32 rows), the
+// whole line otherwise (y blocks of 16, at most 256 of them); x-pass box: the
+// largest of L, 256 or L / 2 that divides L and is at most 256
+__host__ __device__ constexpr int ybox(int R1, int L) { return R1 == 32 ? (L < 256 ? L : 256) : L; }
+__host__ __device__ constexpr int xbox(int L) { return L <= 256 ? L : (L % 256 == 0 ? 256 : L / 2); }
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -122,11 +175,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // ------------------------------------------------ z pass: C2R, c^3 - c, R2C
-template <int TP, int NTZ, bool GS>
+template <int R1, int TP, int NTZ, bool GS>
 __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int ntiles) {
     // GS (Allen-Cahn): also sum g(c) - g(cbar) over the grid, FP32 per thread and
     // tile, FP64 across tiles, one FP64 partial per CTA in a.gsum[blockIdx.x]
-    constexpr int M = 32 * TP, NB = 32 / TP, RPC = NTZ / TP, RS = M + TP;
+    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, RS = M + TP;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp, Zh = a.Zp / 2;
     // row stride of the shared tile: >= Zp and RS, and = TP (mod 16) so that the
@@ -139,10 +192,11 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
     float2* tA = buf + RPC * BS;                      // [M] complex FFT twiddles (n2 ownership)
     float2* tB = tA + M;                              // [M] (block ownership)
     float2* rtws = tB + M;                            // [M + 1] real-transform twiddles
+    float2* xz = rtws + M + 1;                        // [RPC][M] R2C partner rows (R1 != 32)
     const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    fill_twiddles<TP>(tA, tB, a.tw, NTZ);
+    fill_twiddles<R1, TP>(tA, tB, a.tw, NTZ);
     for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
     auto issue = [&](int tl) {
         const long long row0 = (long long)tl * RPC;
@@ -168,9 +222,9 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
         cp_wait<0>();
         __syncthreads();
         // C2R pre-processing: Z[k] = (X_k + conj X_{M-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{M-k})
-        float2 v[32];
+        float2 v[R1];
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) {
+        for (int n1 = 0; n1 < R1; ++n1) {
             const int k = n2 + TP * n1;
             float2 xk = buf[r * BS + k], xm = buf[r * BS + (M - k)];
             if (k == 0) {
@@ -183,16 +237,16 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
         }
         __syncthreads();  // tile read: buf becomes transpose space
         // inverse complex FFT of length M
-        Dft<32, 1>::run(v);
-        twiddle_a<TP, 1>(v, n2, tA);
+        Dft<R1, 1>::run(v);
+        twiddle_a<R1, TP, 1>(v, n2, tA);
 #pragma unroll
-        for (int aa = 0; aa < 32; ++aa) buf[slot(r, n2, aa)] = v[aa];
+        for (int aa = 0; aa < R1; ++aa) buf[slot(r, n2, aa)] = v[aa];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) v[i * TP + c] = buf[slot(r, c, n2 * NB + i)];
-        pass_b<TP, 1>(v);
+        pass_b<R1, TP, 1>(v);
         // real-space samples z[m] = c[2m] + i c[2m+1], m = k1 + 32 k2
         const long long row = row0 + r;
         const bool rowok = row < a.nrows;
@@ -204,7 +258,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
                 const float2 z = v[i * TP + c];
                 const float d0 = z.x * s, d1 = z.y * s;  // c - cbar (the state has no k = 0 mode)
                 if (a.rout && rowok)
-                    reinterpret_cast<float2*>(a.rout + row * a.rpitch)[n2 * NB + i + 32 * c] =
+                    reinterpret_cast<float2*>(a.rout + row * a.rpitch)[n2 * NB + i + R1 * c] =
                         make_float2(fmaf(z.x, s, cbl) + cb, fmaf(z.y, s, cbl) + cb);
                 // g(c) - g(cbar) = d (g'(cbar) + d (3 cbar + d)); the constant g(cbar) only
                 // feeds the k = 0 mode, which the update multiplies by b(0) = 0
@@ -213,8 +267,8 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
             }
         if (GS) gacc += (double)gtile;
         // forward complex FFT of length M from block ownership (m = a + 32 b)
-        pass_b<TP, -1>(v);
-        twiddle_b<TP, -1>(v, n2, tB);
+        pass_b<R1, TP, -1>(v);
+        twiddle_b<R1, TP, -1>(v, n2, tB);
         __syncthreads();  // block-ownership reads of the first transpose done
 #pragma unroll
         for (int i = 0; i < NB; ++i)
@@ -222,30 +276,12 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
             for (int c = 0; c < TP; ++c) buf[slot(r, c, n2 * NB + i)] = v[i * TP + c];
         __syncthreads();
 #pragma unroll
-        for (int aa = 0; aa < 32; ++aa) v[aa] = buf[slot(r, n2, aa)];
+        for (int aa = 0; aa < R1; ++aa) v[aa] = buf[slot(r, n2, aa)];
         __syncthreads();  // buf free: fetch the next tile while this one finishes
         if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
-        Dft<32, -1>::run(v);
-        // R2C post-processing from registers: thread n2 holds Z[n2 + TP d]; the
-        // partner Z[M - k] of k = n2 + TP d sits in thread TP - n2 at index
-        // 31 - d (thread 0: its own index 32 - d), fetched by warp shuffle.
-        //   X_k = (Z_k + conj Z_{M-k})/2 - i e^{-2 pi i k/nz} (Z_k - conj Z_{M-k})/2
-        const int lane = threadIdx.x & 31;
-        const int src = (lane & ~(TP - 1)) | ((TP - n2) & (TP - 1));
-        float2* out = a.out + row * Zp;
-#pragma unroll
-        for (int d = 0; d < 32; ++d) {
-            float2 zm;
-            zm.x = __shfl_sync(0xffffffffu, v[31 - d].x, src);
-            zm.y = __shfl_sync(0xffffffffu, v[31 - d].y, src);
-            if (n2 == 0) zm = v[(32 - d) & 31];
-            const float2 zk = v[d];
-            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-            const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
-            const int k = n2 + TP * d;
-            if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
-        }
-        if (rowok && n2 == 0) out[M] = make_float2(v[0].x - v[0].y, 0.f);  // X_M = Re Z_0 - Im Z_0
+        Dft<R1, -1>::run(v);
+        // R2C post-processing (partner exchange by warp shuffle or the shared row xz)
+        r2c_store<R1, TP>(v, n2, xz + r * M, a.out + row * Zp, rowok, rtws);
     }
     if (GS) {  // fixed-order CTA reduction of the FP64 sums
         __shared__ double red[NTZ / 32];
@@ -270,9 +306,9 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
 // y-blocked spectrum is caller row user_row(r)), pitch a.rpitch floats.
 
 // R2C: real rows (minus the FP64 mean when a.cbar) -> complex rows a.out
-template <int TP, int NTZ>
+template <int R1, int TP, int NTZ>
 __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int ntiles) {
-    constexpr int M = 32 * TP, NB = 32 / TP, RPC = NTZ / TP, RS = M + TP;
+    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, RS = M + TP;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp;
     const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
@@ -280,10 +316,11 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int n
     float2* tA = buf + RPC * BS;
     float2* tB = tA + M;
     float2* rtws = tB + M;
+    float2* xz = rtws + M + 1;  // [RPC][M] R2C partner rows (R1 != 32)
     const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    fill_twiddles<TP>(tA, tB, a.tw, NTZ);
+    fill_twiddles<R1, TP>(tA, tB, a.tw, NTZ);
     for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
     auto issue = [&](int tl) {
         const long long row0 = (long long)tl * RPC;
@@ -307,12 +344,12 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int n
         cp_wait<0>();
         __syncthreads();
         // samples z[m] = c[2m] + i c[2m+1] in block ownership (m = n2 NB + i + 32 c)
-        float2 v[32];
+        float2 v[R1];
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) {
-                float2 z = buf[r * BS + n2 * NB + i + 32 * c];
+                float2 z = buf[r * BS + n2 * NB + i + R1 * c];
                 if (sub) {  // (x - hi) - lo: x - hi is exact for x within a factor 2 of hi
                     z.x = (z.x - hi) - lo;
                     z.y = (z.y - hi) - lo;
@@ -320,45 +357,30 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int n
                 v[i * TP + c] = z;
             }
         __syncthreads();  // rows read: buf becomes transpose space
-        pass_b<TP, -1>(v);
-        twiddle_b<TP, -1>(v, n2, tB);
+        pass_b<R1, TP, -1>(v);
+        twiddle_b<R1, TP, -1>(v, n2, tB);
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) buf[slot(r, c, n2 * NB + i)] = v[i * TP + c];
         __syncthreads();
 #pragma unroll
-        for (int aa = 0; aa < 32; ++aa) v[aa] = buf[slot(r, n2, aa)];
+        for (int aa = 0; aa < R1; ++aa) v[aa] = buf[slot(r, n2, aa)];
         __syncthreads();  // buf free: fetch the next tile while this one finishes
         if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
-        Dft<32, -1>::run(v);
-        // R2C post-processing from registers, partner by warp shuffle (as in the z step)
+        Dft<R1, -1>::run(v);
+        // R2C post-processing (as in the z step)
         const long long row = row0 + r;
         const bool rowok = row < a.nrows;
-        const int lane = threadIdx.x & 31;
-        const int src = (lane & ~(TP - 1)) | ((TP - n2) & (TP - 1));
-        float2* out = a.out + row * Zp;
-#pragma unroll
-        for (int d = 0; d < 32; ++d) {
-            float2 zm;
-            zm.x = __shfl_sync(0xffffffffu, v[31 - d].x, src);
-            zm.y = __shfl_sync(0xffffffffu, v[31 - d].y, src);
-            if (n2 == 0) zm = v[(32 - d) & 31];
-            const float2 zk = v[d];
-            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-            const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
-            const int k = n2 + TP * d;
-            if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
-        }
-        if (rowok && n2 == 0) out[M] = make_float2(v[0].x - v[0].y, 0.f);  // X_M = Re Z_0 - Im Z_0
+        r2c_store<R1, TP>(v, n2, xz + r * M, a.out + row * Zp, rowok, rtws);
     }
 }
 
 // C2R: complex rows a.in -> real rows c = z / (ny nz) + cbar; ACC adds to the
 // rows instead; PART: FP64 partial per CTA of sum (c^2 - 1)^2 in a.partials
-template <int TP, int NTZ, bool ACC, bool PART>
+template <int R1, int TP, int NTZ, bool ACC, bool PART>
 __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int ntiles) {
-    constexpr int M = 32 * TP, NB = 32 / TP, RPC = NTZ / TP, RS = M + TP;
+    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, RS = M + TP;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp, Zh = a.Zp / 2;
     const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
@@ -370,7 +392,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int n
     int tile = blockIdx.x;
     double acc = 0.0;
     if (tile < ntiles) {
-        fill_twiddles<TP>(tA, tB, a.tw, NTZ);
+        fill_twiddles<R1, TP>(tA, tB, a.tw, NTZ);
         for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
     }
     auto issue = [&](int tl) {
@@ -393,9 +415,9 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int n
         cp_wait<0>();
         __syncthreads();
         // C2R pre-processing: Z[k] = (X_k + conj X_{M-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{M-k})
-        float2 v[32];
+        float2 v[R1];
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) {
+        for (int n1 = 0; n1 < R1; ++n1) {
             const int k = n2 + TP * n1;
             float2 xk = buf[r * BS + k], xm = buf[r * BS + (M - k)];
             if (k == 0) {
@@ -407,23 +429,23 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int n
             v[n1] = cadd(A, mul_i<1>(cmul(cconj(rtws[k]), B)));
         }
         __syncthreads();  // tile read: buf becomes transpose space
-        Dft<32, 1>::run(v);
-        twiddle_a<TP, 1>(v, n2, tA);
+        Dft<R1, 1>::run(v);
+        twiddle_a<R1, TP, 1>(v, n2, tA);
 #pragma unroll
-        for (int aa = 0; aa < 32; ++aa) buf[slot(r, n2, aa)] = v[aa];
+        for (int aa = 0; aa < R1; ++aa) buf[slot(r, n2, aa)] = v[aa];
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) v[i * TP + c] = buf[slot(r, c, n2 * NB + i)];
-        pass_b<TP, 1>(v);
+        pass_b<R1, TP, 1>(v);
         __syncthreads();  // transpose reads done: buf stages the real rows in natural order
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) {
                 const float2 z = v[i * TP + c];
-                buf[r * BS + n2 * NB + i + 32 * c] = make_float2(fmaf(z.x, s, cbl) + cb, fmaf(z.y, s, cbl) + cb);
+                buf[r * BS + n2 * NB + i + R1 * c] = make_float2(fmaf(z.x, s, cbl) + cb, fmaf(z.y, s, cbl) + cb);
             }
         __syncthreads();
         for (int e = threadIdx.x; e < RPC * (M / 2); e += NTZ) {  // coalesced 16-byte stores
@@ -550,11 +572,11 @@ __device__ __forceinline__ void fence_async_smem() {
 
 // y pass with TMA: boxes {8, 32 (y in block), 1 (x), BOX/32 (y blocks)} cover
 // BOX consecutive y rows of one x line (y blocks of 32 rows)
-template <int TP, int DIR>
+template <int R1, int TP, int DIR>
 __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int ntiles,
                                                             const __grid_constant__ CUtensorMap min,
                                                             const __grid_constant__ CUtensorMap mout) {
-    constexpr int L = 32 * TP, NB = 32 / TP, XB = (L + TP) * 8, BOX = L < 256 ? L : 256, NBOX = L / BOX;
+    constexpr int L = R1 * TP, NB = R1 / TP, XB = (L + TP) * 8, BOX = ybox(R1, L), NBOX = L / BOX;
     extern __shared__ __align__(1024) float4 smem4[];
     float2* buf = reinterpret_cast<float2*>(smem4);  // [L][8] TMA destination
     float2* xb = buf + L * 8;                         // transpose, then store staging
@@ -565,7 +587,7 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
     const int nchunks = a.nchunks;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    fill_twiddles<TP>(tA, tB, a.tw, 8 * TP);
+    fill_twiddles<R1, TP>(tA, tB, a.tw, 8 * TP);
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -577,36 +599,36 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
         fence_async_smem();
         mbar_expect_tx(bar, L * 8 * sizeof(float2));
 #pragma unroll
-        for (int b = 0; b < NBOX; ++b) tma_load4(buf + b * BOX * 8, &min, chunk * 8, 0, outer, b * BOX / 32, bar);
+        for (int b = 0; b < NBOX; ++b) tma_load4(buf + b * BOX * 8, &min, chunk * 8, 0, outer, b * BOX / a.YB, bar);
     };
     if (threadIdx.x == 0) issue(tile);
     uint32_t parity = 0;
     for (; tile < ntiles; tile += gridDim.x) {
         mbar_wait_or_abort(bar, parity, &s_abort);
         parity ^= 1;
-        float2 v[32];
+        float2 v[R1];
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) v[n1] = buf[(n2 + TP * n1) * 8 + p];
+        for (int n1 = 0; n1 < R1; ++n1) v[n1] = buf[(n2 + TP * n1) * 8 + p];
         if (threadIdx.x == 0) bulk_wait_read0();  // previous store has left the staging tile
         __syncthreads();
         const int next = tile + gridDim.x;
         if (threadIdx.x == 0 && next < ntiles) issue(next);
-        Dft<32, DIR>::run(v);
-        twiddle_a<TP, DIR>(v, n2, tA);
-        t1_s<TP, 8>(v, xb, n2, p);
-        pass_b<TP, DIR>(v);
+        Dft<R1, DIR>::run(v);
+        twiddle_a<R1, TP, DIR>(v, n2, tA);
+        t1_s<R1, TP, 8>(v, xb, n2, p);
+        pass_b<R1, TP, DIR>(v);
         __syncthreads();  // transpose reads done: xb becomes the store staging tile
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
-            for (int c = 0; c < TP; ++c) xb[(n2 * NB + i + 32 * c) * 8 + p] = v[i * TP + c];
+            for (int c = 0; c < TP; ++c) xb[(n2 * NB + i + R1 * c) * 8 + p] = v[i * TP + c];
         fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
             const int outer = tile / nchunks, chunk = tile - outer * nchunks;
 #pragma unroll
             for (int b = 0; b < NBOX; ++b)
-                tma_store4(&mout, chunk * 8, 0, outer, b * BOX / 32, xb + b * BOX * 8);
+                tma_store4(&mout, chunk * 8, 0, outer, b * BOX / a.YB, xb + b * BOX * 8);
             bulk_commit();
         }
     }
@@ -616,12 +638,13 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
 // x pass + update with TMA: boxes {8, 1, BOX (x), 1}. MODE 0: Cahn-Hilliard,
 // 1: Allen-Cahn, 2: preconditioner only (S' = F_x^-1 (dt / (1 + dt M0 kappa |k|^4)
 // F_x W), S not read; the variable-mobility model's spectral step)
-template <int TP, int MODE>
+template <int R1, int TP, int MODE>
 __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int ntiles,
                                                               const __grid_constant__ CUtensorMap mW,
                                                               const __grid_constant__ CUtensorMap mS,
                                                               const __grid_constant__ CUtensorMap mO) {
-    constexpr int L = 32 * TP, NB = 32 / TP, XB = (L + TP) * 8, BOX = L < 256 ? L : 256, NBOX = L / BOX;
+    constexpr int L = R1 * TP, NB = R1 / TP, XB = (L + TP) * 8, BOX = xbox(L), NBOX = L / BOX;
+    static_assert(L % BOX == 0 && BOX <= 256, "x-pass TMA box");
     extern __shared__ __align__(1024) float4 smem4[];
     float2* bufW = reinterpret_cast<float2*>(smem4);
     float2* bufS = bufW + L * 8;
@@ -634,7 +657,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
     const int nchunks = a.nchunks;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    fill_twiddles<TP>(tA, tB, a.tw, 8 * TP);
+    fill_twiddles<R1, TP>(tA, tB, a.tw, 8 * TP);
     for (int i = threadIdx.x; i < L; i += 8 * TP) k2xs[i] = a.k2x[i];
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
@@ -664,25 +687,25 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         const int next = tile + gridDim.x;
         // ---- g_hat = F_x W, kept as G = -dt M |k|^2 g_hat (Allen-Cahn: -dt L g_hat)
         mbar_wait_or_abort(bars + 0, parity, &s_abort);
-        float2 v[32];
+        float2 v[R1];
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufW[(n2 + TP * n1) * 8 + p];
+        for (int n1 = 0; n1 < R1; ++n1) v[n1] = bufW[(n2 + TP * n1) * 8 + p];
         if (threadIdx.x == 0) bulk_wait_read0();
         __syncthreads();
         if (threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
-        Dft<32, -1>::run(v);
-        twiddle_a<TP, -1>(v, n2, tA);
-        t1_s<TP, 8>(v, xb, n2, p);
-        pass_b<TP, -1>(v);
+        Dft<R1, -1>::run(v);
+        twiddle_a<R1, TP, -1>(v, n2, tA);
+        t1_s<R1, TP, 8>(v, xb, n2, p);
+        pass_b<R1, TP, -1>(v);
         const int kz = chunk * 8 + p;
         const bool valid = kz < a.ncols;
         const float k2yz = a.k2y[ky] + (valid ? a.k2z[kz] : 0.f);
-        float2 G[32];
+        float2 G[R1];
 #pragma unroll
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) {
-                const float k2g = k2xs[n2 * NB + i + 32 * c] + k2yz;
+                const float k2g = k2xs[n2 * NB + i + R1 * c] + k2yz;
                 const float f = PRE  ? a.dtM * a.invL * rcp_approx(fmaf(a.dtMk, k2g * k2g, 1.f))
                                 : AC ? ndtM
                                      : ndtM * k2g;
@@ -691,40 +714,40 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         if (PRE) {
             parity ^= 1;
 #pragma unroll
-            for (int q = 0; q < 32; ++q) v[q] = G[q];
+            for (int q = 0; q < R1; ++q) v[q] = G[q];
         } else {
             // ---- c_hat = F_x S
             mbar_wait_or_abort(bars + 1, parity, &s_abort);
             parity ^= 1;
 #pragma unroll
-            for (int n1 = 0; n1 < 32; ++n1) v[n1] = bufS[(n2 + TP * n1) * 8 + p];
+            for (int n1 = 0; n1 < R1; ++n1) v[n1] = bufS[(n2 + TP * n1) * 8 + p];
             __syncthreads();
             if (threadIdx.x == 0 && next < ntiles) issue(&mS, bufS, bars + 1, next);
-            Dft<32, -1>::run(v);
-            twiddle_a<TP, -1>(v, n2, tA);
-            t1_s<TP, 8>(v, xb, n2, p);
-            pass_b<TP, -1>(v);
+            Dft<R1, -1>::run(v);
+            twiddle_a<R1, TP, -1>(v, n2, tA);
+            t1_s<R1, TP, 8>(v, xb, n2, p);
+            pass_b<R1, TP, -1>(v);
             // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L; k = 0 stays out
             //      (Allen-Cahn: (c_hat - dt L g_hat) / (1 + dt L kappa |k|^2) / L)
 #pragma unroll
             for (int i = 0; i < NB; ++i)
 #pragma unroll
                 for (int c = 0; c < TP; ++c) {
-                    const float k2 = k2xs[n2 * NB + i + 32 * c] + k2yz;
+                    const float k2 = k2xs[n2 * NB + i + R1 * c] + k2yz;
                     const float f = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
                     v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), f);
                 }
         }
         if (ky == 0 && kz == 0 && n2 == 0) v[0] = make_float2(0.f, 0.f);
         // ---- S' = F_x^-1 c_hat'
-        pass_b<TP, 1>(v);
-        twiddle_b<TP, 1>(v, n2, tB);
+        pass_b<R1, TP, 1>(v);
+        twiddle_b<R1, TP, 1>(v, n2, tB);
         __syncthreads();
-        t2_s<TP, 8>(v, xb, n2, p);
-        Dft<32, 1>::run(v);
+        t2_s<R1, TP, 8>(v, xb, n2, p);
+        Dft<R1, 1>::run(v);
         __syncthreads();  // transpose reads done: xb becomes the store staging tile
 #pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) xb[(n2 + TP * n1) * 8 + p] = v[n1];
+        for (int n1 = 0; n1 < R1; ++n1) xb[(n2 + TP * n1) * 8 + p] = v[n1];
         fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -781,18 +804,6 @@ static cudaError_t prep(K kernel, size_t smem, int threads, int* grid_per_sm) {
     return cudaSuccess;
 }
 
-static int tp_of(int L) {
-    switch (L) {
-        case 64: return 2;
-        case 128: return 4;
-        case 256: return 8;
-        case 512: return 16;
-        case 1024: return 32;
-        default: return 0;
-    }
-}
-
-
 // ------------------------------------------------------- tensor maps (host)
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -837,33 +848,34 @@ bool fast_timeout_flag(int* flag, bool clear) {
     return true;
 }
 
-template <int TP, int DIR>
+template <int R1, int TP, int DIR>
 static bool run_fspass_tma(const SPassArgs& a, cudaStream_t st, cudaError_t* err) {
-    constexpr int L = 32 * TP, BOX = L < 256 ? L : 256;
-    // y pass geometry: rows y split in blocks of 32 (rs = Zp), lines x (os = 32 Zp)
-    if (a.YB != 32 || a.rs * 32 != a.os) return false;
+    constexpr int L = R1 * TP, BOX = fast::ybox(R1, L);
+    // y pass geometry: rows y split in blocks of YB (rs = Zp), lines x (os = YB Zp);
+    // a box covers YB rows of BOX / YB consecutive blocks
+    if (a.rs * a.YB != a.os || a.YB > 256 || BOX % a.YB || BOX / a.YB > 256) return false;
     const long long Zp = a.rs;
     CUtensorMap mi, mo;
-    if (!make_map(&mi, a.in, a.ncols, 32, a.nouter, a.L, Zp, 32, 1, BOX / 32) ||
-        !make_map(&mo, a.out, a.ncols, 32, a.nouter, a.L, Zp, 32, 1, BOX / 32))
+    if (!make_map(&mi, a.in, a.ncols, a.YB, a.nouter, a.L, Zp, a.YB, 1, BOX / a.YB) ||
+        !make_map(&mo, a.out, a.ncols, a.YB, a.nouter, a.L, Zp, a.YB, 1, BOX / a.YB))
         return false;
     const size_t smem = sizeof(float2) * (L * 8 + (L + TP) * 8 + 2 * L) + 16;
     int per = 0;
-    cudaError_t e = prep(fast::fspass_tma_kernel<TP, DIR>, smem, 8 * TP, &per);
+    cudaError_t e = prep(fast::fspass_tma_kernel<R1, TP, DIR>, smem, 8 * TP, &per);
     if (e != cudaSuccess) {
         *err = e;
         return true;
     }
     const int ntiles = a.nchunks * a.nouter;
     const int grid = std::min(ntiles, per * num_sms());
-    fast::fspass_tma_kernel<TP, DIR><<<grid, 8 * TP, smem, st>>>(a, ntiles, mi, mo);
+    fast::fspass_tma_kernel<R1, TP, DIR><<<grid, 8 * TP, smem, st>>>(a, ntiles, mi, mo);
     *err = cudaGetLastError();
     return true;
 }
 
-template <int TP>
+template <int R1, int TP>
 static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
-    constexpr int L = 32 * TP, BOX = L < 256 ? L : 256;
+    constexpr int L = R1 * TP, BOX = fast::xbox(L);
     // x pass geometry: rows x (rs = YB Zp), lines y split in blocks of YB (os = Zp)
     if (a.os * a.YB != a.rs) return false;
     const long long Zp = a.os;
@@ -874,9 +886,9 @@ static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) 
         return false;
     const size_t smem = sizeof(float2) * (2 * L * 8 + (L + TP) * 8 + 2 * L) + sizeof(float) * L + 16;
     int per = 0;
-    auto kern = a.model == 2   ? fast::fxupd_tma_kernel<TP, 2>
-                : a.model == 1 ? fast::fxupd_tma_kernel<TP, 1>
-                               : fast::fxupd_tma_kernel<TP, 0>;
+    auto kern = a.model == 2   ? fast::fxupd_tma_kernel<R1, TP, 2>
+                : a.model == 1 ? fast::fxupd_tma_kernel<R1, TP, 1>
+                               : fast::fxupd_tma_kernel<R1, TP, 0>;
     cudaError_t e = prep(kern, smem, 8 * TP, &per);
     if (e != cudaSuccess) {
         *err = e;
@@ -890,38 +902,49 @@ static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) 
 }
 
 bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err) {
-    const int TP = tp_of(a.L);
-    if (!TP) return false;
-#define CASE(T)                                                                       \
-    case T:                                                                           \
-        return dir < 0 ? run_fspass_tma<T, -1>(a, st, err) : run_fspass_tma<T, 1>(a, st, err);
-    switch (TP) {
-        CASE(2) CASE(4) CASE(8) CASE(16) CASE(32)
+#define CASE(L, R, T)                                                                       \
+    case L:                                                                                 \
+        return dir < 0 ? run_fspass_tma<R, T, -1>(a, st, err) : run_fspass_tma<R, T, 1>(a, st, err);
+    switch (a.L) {
+        CASE(64, 32, 2) CASE(128, 32, 4) CASE(256, 32, 8) CASE(512, 32, 16) CASE(1024, 32, 32) CASE(400, 20, 20)
     }
 #undef CASE
     return false;
 }
 
 bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
-    const int TP = tp_of(a.L);
-    if (!TP || a.W == nullptr) return false;
-    switch (TP) {
-        case 2: return run_fxupd_tma<2>(a, st, err);
-        case 4: return run_fxupd_tma<4>(a, st, err);
-        case 8: return run_fxupd_tma<8>(a, st, err);
-        case 16: return run_fxupd_tma<16>(a, st, err);
-        case 32: return run_fxupd_tma<32>(a, st, err);
+    if (a.W == nullptr) return false;
+    switch (a.L) {
+        case 64: return run_fxupd_tma<32, 2>(a, st, err);
+        case 128: return run_fxupd_tma<32, 4>(a, st, err);
+        case 256: return run_fxupd_tma<32, 8>(a, st, err);
+        case 512: return run_fxupd_tma<32, 16>(a, st, err);
+        case 1024: return run_fxupd_tma<32, 32>(a, st, err);
+        case 400: return run_fxupd_tma<20, 20>(a, st, err);
     }
     return false;
 }
 
-template <int TP>
+// threads of a z-pass CTA: 128 for R1 = 32, 160 (16 rows of 10 threads) for R1 = 20
+template <int R1, int TP>
+constexpr int ntz_of() {
+    return R1 == 32 ? 128 : 160;
+}
+// shared memory of a z-pass CTA: the row tile, three twiddle tables and, for
+// R1 != 32, the R2C partner rows (as laid out in the kernels)
+template <int R1, int TP>
+static size_t zpass_smem(int Zp) {
+    constexpr int NTZ = ntz_of<R1, TP>(), RPC = NTZ / TP, M = R1 * TP, RS = M + TP;
+    const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
+    return sizeof(float2) * ((size_t)RPC * BS + 3 * M + 1 + (R1 != 32 ? (size_t)RPC * M : 0));
+}
+
+template <int R1, int TP>
 static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st, int* grid_used) {
-    constexpr int NTZ = 128, RPC = NTZ / TP, RS = 32 * TP + TP;
-    const int BS = TP + (((a.Zp > RS ? a.Zp : RS) - TP + 15) & ~15);  // as in the kernel
-    const size_t smem = sizeof(float2) * ((size_t)RPC * BS + 3 * 32 * TP + 1);
+    constexpr int NTZ = ntz_of<R1, TP>(), RPC = NTZ / TP;
+    const size_t smem = zpass_smem<R1, TP>(a.Zp);
     int per = 0;
-    auto kern = a.gsum ? fast::fzstep_kernel<TP, NTZ, true> : fast::fzstep_kernel<TP, NTZ, false>;
+    auto kern = a.gsum ? fast::fzstep_kernel<R1, TP, NTZ, true> : fast::fzstep_kernel<R1, TP, NTZ, false>;
     cudaError_t e = prep(kern, smem, NTZ, &per);
     if (e != cudaSuccess) return e;
     const int ntiles = (int)((a.nrows + RPC - 1) / RPC);
@@ -931,19 +954,18 @@ static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st, int* grid_use
     return cudaGetLastError();
 }
 
-template <int TP>
+template <int R1, int TP>
 static cudaError_t run_fzconv(const ZPassArgs& a, int dir, cudaStream_t st, int* grid_used) {
-    constexpr int NTZ = 128, RPC = NTZ / TP, RS = 32 * TP + TP;
-    const int BS = TP + (((a.Zp > RS ? a.Zp : RS) - TP + 15) & ~15);  // as in the kernels
-    const size_t smem = sizeof(float2) * ((size_t)RPC * BS + 3 * 32 * TP + 1);
+    constexpr int NTZ = ntz_of<R1, TP>(), RPC = NTZ / TP;
+    const size_t smem = zpass_smem<R1, TP>(a.Zp);
     const int ntiles = (int)((a.nrows + RPC - 1) / RPC);
     void (*kern)(ZPassArgs, int);
     if (dir < 0)
-        kern = fast::fr2c_kernel<TP, NTZ>;
+        kern = fast::fr2c_kernel<R1, TP, NTZ>;
     else if (a.accumulate)
-        kern = a.partials ? fast::fc2r_kernel<TP, NTZ, true, true> : fast::fc2r_kernel<TP, NTZ, true, false>;
+        kern = a.partials ? fast::fc2r_kernel<R1, TP, NTZ, true, true> : fast::fc2r_kernel<R1, TP, NTZ, true, false>;
     else
-        kern = a.partials ? fast::fc2r_kernel<TP, NTZ, false, true> : fast::fc2r_kernel<TP, NTZ, false, false>;
+        kern = a.partials ? fast::fc2r_kernel<R1, TP, NTZ, false, true> : fast::fc2r_kernel<R1, TP, NTZ, false, false>;
     int per = 0;
     cudaError_t e = prep(kern, smem, NTZ, &per);
     if (e != cudaSuccess) return e;
@@ -955,27 +977,25 @@ static cudaError_t run_fzconv(const ZPassArgs& a, int dir, cudaStream_t st, int*
 
 // z R2C (dir < 0) or C2R (dir > 0) alone; false when the fast kernels do not apply
 bool fast_zconv(const ZPassArgs& a, int dir, cudaStream_t st, cudaError_t* err, int* grid_used) {
-    const int TP = tp_of(a.M);
-    if (TP < 2 || TP > 16) return false;
     const float* real = dir < 0 ? a.rin : a.rout;
     if (!real || ((uintptr_t)real & 15) || (a.rpitch & 3)) return false;
-    switch (TP) {
-        case 2: *err = run_fzconv<2>(a, dir, st, grid_used); return true;
-        case 4: *err = run_fzconv<4>(a, dir, st, grid_used); return true;
-        case 8: *err = run_fzconv<8>(a, dir, st, grid_used); return true;
-        case 16: *err = run_fzconv<16>(a, dir, st, grid_used); return true;
+    switch (a.M) {
+        case 64: *err = run_fzconv<32, 2>(a, dir, st, grid_used); return true;
+        case 128: *err = run_fzconv<32, 4>(a, dir, st, grid_used); return true;
+        case 256: *err = run_fzconv<32, 8>(a, dir, st, grid_used); return true;
+        case 512: *err = run_fzconv<32, 16>(a, dir, st, grid_used); return true;
+        case 200: *err = run_fzconv<20, 10>(a, dir, st, grid_used); return true;
     }
     return false;
 }
 
 bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used) {
-    const int TP = tp_of(a.M);
-    if (TP < 2 || TP > 16) return false;
-    switch (TP) {
-        case 2: *err = run_fzstep<2>(a, st, grid_used); return true;
-        case 4: *err = run_fzstep<4>(a, st, grid_used); return true;
-        case 8: *err = run_fzstep<8>(a, st, grid_used); return true;
-        case 16: *err = run_fzstep<16>(a, st, grid_used); return true;
+    switch (a.M) {
+        case 64: *err = run_fzstep<32, 2>(a, st, grid_used); return true;
+        case 128: *err = run_fzstep<32, 4>(a, st, grid_used); return true;
+        case 256: *err = run_fzstep<32, 8>(a, st, grid_used); return true;
+        case 512: *err = run_fzstep<32, 16>(a, st, grid_used); return true;
+        case 200: *err = run_fzstep<20, 10>(a, st, grid_used); return true;
     }
     return false;
 }

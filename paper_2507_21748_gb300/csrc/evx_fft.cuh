@@ -232,6 +232,74 @@ struct Dft<5, DIR> {
     }
 };
 
+// multiply by exp(DIR * 2 pi i m / 20) for fixed m (20th roots of unity)
+template <int DIR, int m>
+__device__ __forceinline__ float2 w20(float2 a) {
+    // cos(pi j / 10), j = 0..5
+    constexpr float C[6] = {1.0f, 0.95105651629515357f, 0.80901699437494742f, 0.58778525229247313f,
+                            0.30901699437494742f, 0.0f};
+    constexpr int mm = m % 20;
+    if (mm == 0) return a;
+    if (mm == 5) return mul_i<DIR>(a);
+    if (mm == 10) return make_float2(-a.x, -a.y);
+    if (mm == 15) return mul_i<-DIR>(a);
+    // cos and sin of pi mm / 10 from the first quadrant by symmetry
+    constexpr int q = mm % 10, qq = q <= 5 ? q : 10 - q;
+    constexpr float cq = q <= 5 ? C[qq] : -C[qq];  // cos(pi q / 10)
+    constexpr float sq = C[5 - qq];                // sin(pi q / 10) >= 0
+    constexpr float c = mm < 10 ? cq : -cq, s = mm < 10 ? sq : -sq;
+    const float ds = DIR < 0 ? -s : s;
+    return make_float2(fmaf(a.x, c, -a.y * ds), fmaf(a.x, ds, a.y * c));
+}
+
+// length 10 = 2 x 5, decimation in time: F_r = DFT5(x[2 m + r]),
+// X[k + 5 q] = F_0[k] + (-1)^q w_10^k F_1[k]
+template <int DIR>
+struct Dft<10, DIR> {
+    template <int k>
+    __device__ __forceinline__ static void comb(float2* v, const float2* e, const float2* o) {
+        const float2 t = w20<DIR, 2 * k>(o[k]);
+        v[k] = cadd(e[k], t);
+        v[k + 5] = csub(e[k], t);
+    }
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 e[5], o[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            e[m] = v[2 * m];
+            o[m] = v[2 * m + 1];
+        }
+        Dft<5, DIR>::run(e);
+        Dft<5, DIR>::run(o);
+        comb<0>(v, e, o); comb<1>(v, e, o); comb<2>(v, e, o); comb<3>(v, e, o); comb<4>(v, e, o);
+    }
+};
+
+// length 20 = 4 x 5, decimation in time: F_r = DFT5(x[4 m + r]) (r < 4),
+// X[k + 5 q] = DFT4_r(w_20^{r k} F_r[k])[q]
+template <int DIR>
+struct Dft<20, DIR> {
+    template <int k>
+    __device__ __forceinline__ static void comb(float2* v, float2 (&f)[4][5]) {
+        float2 g0 = f[0][k], g1 = w20<DIR, k>(f[1][k]), g2 = w20<DIR, 2 * k>(f[2][k]), g3 = w20<DIR, 3 * k>(f[3][k]);
+        dft4<DIR>(g0, g1, g2, g3);
+        v[k] = g0;
+        v[k + 5] = g1;
+        v[k + 10] = g2;
+        v[k + 15] = g3;
+    }
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 f[4][5];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) f[r][m] = v[4 * m + r];
+            Dft<5, DIR>::run(f[r]);
+        }
+        comb<0>(v, f); comb<1>(v, f); comb<2>(v, f); comb<3>(v, f); comb<4>(v, f);
+    }
+};
+
 // Tile descriptor: pencil p, element i at buf[i*es + p*ps].
 struct Tile {
     float2* buf;

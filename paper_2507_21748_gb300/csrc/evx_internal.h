@@ -12,7 +12,9 @@ namespace evx {
 // YB = ny otherwise (plain [x][y][kz]). The x stride is then YB * Zp (at most
 // 133 KB at nz = 1024), so the 1024 rows of an x tile share a few 2 MB pages.
 inline int choose_yblock(int ny, bool fast) {
-    return (fast && ny >= 64 && ny <= 1024 && (ny & (ny - 1)) == 0) ? 32 : ny;
+    if (fast && ny >= 64 && ny <= 1024 && (ny & (ny - 1)) == 0) return 32;
+    if (fast && ny == 400) return 16;  // the y pass moves a whole line as one box of 25 blocks
+    return ny;
 }
 // offset of index i along an axis split into blocks of YB: i % YB steps of
 // s_in, i / YB steps of s_out

@@ -49,9 +49,12 @@ def gpu_run(evx, c0, nsteps, **params):
 # threads-per-pencil variant, x, y and z)
 SMALL = [(8, 8, 8), (16, 32, 64), (48, 40, 36), (24, 30, 50), (64, 64, 64)]
 POW2 = [(64, 128, 256), (256, 512, 128), (512, 64, 1024), (1024, 256, 64), (128, 1024, 512)]
+# lengths 400 = 20 x 20 along x and y and nz = 400 (M = 200 = 20 x 10) take the
+# R1 = 20 fast kernels one axis at a time, next to power-of-two axes
+MIXED = [(400, 64, 128), (64, 400, 128), (64, 128, 400)]
 
 
-@pytest.mark.parametrize("shape", SMALL + [(400, 16, 20), (10, 1024, 12)])
+@pytest.mark.parametrize("shape", SMALL + [(400, 16, 20), (10, 1024, 12), (24, 400, 64), (16, 32, 400)])
 def test_roundtrip(evx, shape):
     import torch
     c = inputs.uniform_field(shape, seed=3, offset=0.3)
@@ -64,7 +67,7 @@ def test_roundtrip(evx, shape):
     assert abs(mean - c.astype(np.float64).mean()) < 1e-15
 
 
-@pytest.mark.parametrize("shape", SMALL + POW2 + [(128, 128, 128)])
+@pytest.mark.parametrize("shape", SMALL + POW2 + MIXED + [(128, 128, 128)])
 def test_one_step_vs_oracle(evx, shape):
     c0 = inputs.uniform_field(shape, seed=0)
     ref = O.ch_step(c0, DT, M, KAPPA, H, 1)
@@ -153,13 +156,14 @@ def test_graph_and_profiled_paths_identical(evx):
     assert torch.equal(outs[0], outs[1])
 
 
-def test_fast_and_generic_kernels_agree(evx, tmp_path):
-    """The power-of-two fast kernels and the generic mixed-radix kernels (forced
-    with EVX_GENERIC=1 in a child process) give the same field to FP32 rounding."""
+@pytest.mark.parametrize("shape", [(128, 256, 512), (400, 400, 400)])
+def test_fast_and_generic_kernels_agree(evx, tmp_path, shape):
+    """The fast kernels (R1 = 32 and R1 = 20 four-step splits) and the generic
+    mixed-radix kernels (forced with EVX_GENERIC=1 in a child process) give the
+    same field to FP32 rounding."""
     import subprocess
     import sys
     import torch
-    shape = (128, 256, 512)
     c0 = inputs.uniform_field(shape, seed=8, offset=0.2)
     got = gpu_run(evx, c0, 10)
     script = (
@@ -178,7 +182,7 @@ def test_fast_and_generic_kernels_agree(evx, tmp_path):
     assert rel_l2(got, gen) <= 2e-6
 
 
-@pytest.mark.parametrize("shape", [(32, 48, 40), (64, 128, 40), (24, 256, 64)])
+@pytest.mark.parametrize("shape", [(32, 48, 40), (64, 128, 40), (24, 256, 64), (16, 400, 400)])
 def test_host_io_matches_device_io(evx, shape):
     """Host copies (per y block of the spectral layout) equal the device path."""
     import torch

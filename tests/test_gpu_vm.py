@@ -115,11 +115,11 @@ def test_graph_and_profiled_paths_identical(evx):
     assert torch.equal(outs[0], outs[1])
 
 
-def test_fast_and_generic_kernels_agree(evx, tmp_path):
+@pytest.mark.parametrize("shape", [(128, 256, 128), (400, 400, 400)])
+def test_fast_and_generic_kernels_agree(evx, tmp_path, shape):
     import os
     import subprocess
     import sys
-    shape = (128, 256, 128)
     c0 = inputs.uniform_field(shape, seed=26, offset=0.2)
     got, _, _ = vm_run(evx, c0, 10)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))

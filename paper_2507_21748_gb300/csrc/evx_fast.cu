@@ -168,6 +168,21 @@ __device__ __forceinline__ void r2c_store(const float2 (&v)[R1], int n2, float2*
 __host__ __device__ constexpr int ybox(int R1, int L) { return R1 == 32 ? (L < 256 ? L : 256) : L; }
 __host__ __device__ constexpr int xbox(int L) { return L <= 256 ? L : (L % 256 == 0 ? 256 : L / 2); }
 
+// z-pass transposes: a tile row (one pencil, r = thread / TP) holds slot
+// aa TP + n2 + (aa / NB) ZPAD, the rows BS = TP (mod 16) apart. With the group
+// stride s = R1 + ZPAD odd and (s - 1) TP = 0 (mod 16), thread t = TP r + n2
+// addresses bank pair t (n2 ownership) or s t (block ownership) mod 16: no two
+// threads of a half-warp share a bank. ZPAD = 1 for R1 = 32 (s = 33), 5 for
+// R1 = 20, TP = 10 (s = 25).
+__host__ __device__ constexpr int zpad(int R1, int TP) {
+    for (int d = 1; d < 16; ++d)
+        if (((R1 + d) & 1) && ((R1 + d - 1) * TP) % 16 == 0) return d;
+    return 1;
+}
+// stride of the R2C partner rows xz: M rounded up to = TP (mod 16), so the row
+// writes are conflict-free like the n2-ownership slots
+__host__ __device__ constexpr int zxs(int M, int TP) { return M + (((TP - M) % 16) + 16) % 16; }
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -179,7 +194,7 @@ template <int R1, int TP, int NTZ, bool GS>
 __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int ntiles) {
     // GS (Allen-Cahn): also sum g(c) - g(cbar) over the grid, FP32 per thread and
     // tile, FP64 across tiles, one FP64 partial per CTA in a.gsum[blockIdx.x]
-    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, RS = M + TP;
+    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, ZPAD = zpad(R1, TP), RS = M + TP * ZPAD;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp, Zh = a.Zp / 2;
     // row stride of the shared tile: >= Zp and RS, and = TP (mod 16) so that the
@@ -192,7 +207,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
     float2* tA = buf + RPC * BS;                      // [M] complex FFT twiddles (n2 ownership)
     float2* tB = tA + M;                              // [M] (block ownership)
     float2* rtws = tB + M;                            // [M + 1] real-transform twiddles
-    float2* xz = rtws + M + 1;                        // [RPC][M] R2C partner rows (R1 != 32)
+    float2* xz = rtws + M + 1;                        // [RPC][zxs(M, TP)] R2C partner rows (R1 != 32)
     const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
@@ -215,7 +230,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
     const float gp = (float)(3.0 * cbd * cbd - 1.0);  // g'(cbar)
     const float c3 = (float)(3.0 * cbd);
     const float s = a.scale;
-    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB; };
+    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB * ZPAD; };
     double gacc = 0.0;
     for (; tile < ntiles; tile += gridDim.x) {
         const long long row0 = (long long)tile * RPC;
@@ -281,7 +296,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
         if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
         Dft<R1, -1>::run(v);
         // R2C post-processing (partner exchange by warp shuffle or the shared row xz)
-        r2c_store<R1, TP>(v, n2, xz + r * M, a.out + row * Zp, rowok, rtws);
+        r2c_store<R1, TP>(v, n2, xz + r * zxs(M, TP), a.out + row * Zp, rowok, rtws);
     }
     if (GS) {  // fixed-order CTA reduction of the FP64 sums
         __shared__ double red[NTZ / 32];
@@ -308,7 +323,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
 // R2C: real rows (minus the FP64 mean when a.cbar) -> complex rows a.out
 template <int R1, int TP, int NTZ>
 __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int ntiles) {
-    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, RS = M + TP;
+    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, ZPAD = zpad(R1, TP), RS = M + TP * ZPAD;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp;
     const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
@@ -316,7 +331,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int n
     float2* tA = buf + RPC * BS;
     float2* tB = tA + M;
     float2* rtws = tB + M;
-    float2* xz = rtws + M + 1;  // [RPC][M] R2C partner rows (R1 != 32)
+    float2* xz = rtws + M + 1;  // [RPC][zxs(M, TP)] R2C partner rows (R1 != 32)
     const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
@@ -338,7 +353,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int n
     const double cbd = a.cbar ? *a.cbar : 0.0;
     const float hi = (float)cbd, lo = (float)(cbd - (double)hi);
     const bool sub = a.cbar != nullptr;
-    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB; };
+    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB * ZPAD; };
     for (; tile < ntiles; tile += gridDim.x) {
         const long long row0 = (long long)tile * RPC;
         cp_wait<0>();
@@ -372,7 +387,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int n
         // R2C post-processing (as in the z step)
         const long long row = row0 + r;
         const bool rowok = row < a.nrows;
-        r2c_store<R1, TP>(v, n2, xz + r * M, a.out + row * Zp, rowok, rtws);
+        r2c_store<R1, TP>(v, n2, xz + r * zxs(M, TP), a.out + row * Zp, rowok, rtws);
     }
 }
 
@@ -380,7 +395,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int n
 // rows instead; PART: FP64 partial per CTA of sum (c^2 - 1)^2 in a.partials
 template <int R1, int TP, int NTZ, bool ACC, bool PART>
 __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int ntiles) {
-    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, RS = M + TP;
+    constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, ZPAD = zpad(R1, TP), RS = M + TP * ZPAD;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp, Zh = a.Zp / 2;
     const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
@@ -409,7 +424,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int n
     const double cbd = a.cbar ? *a.cbar : 0.0;
     const float cb = (float)cbd, cbl = (float)(cbd - (double)cb);
     const float s = a.scale;
-    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB; };
+    auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB * ZPAD; };
     for (; tile < ntiles; tile += gridDim.x) {
         const long long row0 = (long long)tile * RPC;
         cp_wait<0>();
@@ -934,9 +949,9 @@ constexpr int ntz_of() {
 // R1 != 32, the R2C partner rows (as laid out in the kernels)
 template <int R1, int TP>
 static size_t zpass_smem(int Zp) {
-    constexpr int NTZ = ntz_of<R1, TP>(), RPC = NTZ / TP, M = R1 * TP, RS = M + TP;
+    constexpr int NTZ = ntz_of<R1, TP>(), RPC = NTZ / TP, M = R1 * TP, RS = M + TP * fast::zpad(R1, TP);
     const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
-    return sizeof(float2) * ((size_t)RPC * BS + 3 * M + 1 + (R1 != 32 ? (size_t)RPC * M : 0));
+    return sizeof(float2) * ((size_t)RPC * BS + 3 * M + 1 + (R1 != 32 ? (size_t)RPC * fast::zxs(M, TP) : 0));
 }
 
 template <int R1, int TP>

@@ -461,11 +461,12 @@ def main():
 
     # roofline of the dominant pass
     names = ["x pass + k-space update", "y inverse", "z C2R + c^3-c + R2C", "y forward"]
-    fast = n in (64, 128, 256, 512, 1024) and os.environ.get("EVX_GENERIC", "") != "1"
-    tp = max(n // 32, 2)
-    kern = (["fast::fxupd_tma_kernel<%d>" % tp, "fast::fspass_tma_kernel<%d, 1>" % tp,
-             "fast::fzstep_kernel<%d, 128>" % max(tp // 2, 2), "fast::fspass_tma_kernel<%d, -1>" % tp] if fast else
-            ["xupdate_kernel", "spass_kernel<1>", "zpass_kernel<Z_STEP>", "spass_kernel<-1>"])
+    fast = n in (64, 128, 256, 512, 1024, 400) and os.environ.get("EVX_GENERIC", "") != "1"
+    r1, tp = (20, 20) if n == 400 else (32, max(n // 32, 2))  # four-step split n = R1 x TP
+    rz, tz, ntz = (20, 10, 160) if n == 400 else (32, max(tp // 2, 2), 128)  # z pass: M = n / 2
+    kern = (["fast::fxupd_tma_kernel<%d, %d>" % (r1, tp), "fast::fspass_tma_kernel<%d, %d, 1>" % (r1, tp),
+             "fast::fzstep_kernel<%d, %d, %d>" % (rz, tz, ntz), "fast::fspass_tma_kernel<%d, %d, -1>" % (r1, tp)]
+            if fast else ["xupdate_kernel", "spass_kernel<1>", "zpass_kernel<Z_STEP>", "spass_kernel<-1>"])
     dom = max(range(4), key=lambda k: pass_ms[k])
     avg_ms = pass_ms[dom] / max(pass_cnt[dom], 1)
     alg_bytes = g.pass_bytes(dom)

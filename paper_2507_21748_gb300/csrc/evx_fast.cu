@@ -650,30 +650,41 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
     if (threadIdx.x == 0) bulk_wait0();
 }
 
-// x pass + update with TMA: boxes {8, 1, BOX (x), 1}. MODE 0: Cahn-Hilliard,
-// 1: Allen-Cahn, 2: preconditioner only (S' = F_x^-1 (dt / (1 + dt M0 kappa |k|^4)
-// F_x W), S not read; the variable-mobility model's spectral step)
-template <int R1, int TP, int MODE>
-__global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int ntiles,
-                                                              const __grid_constant__ CUtensorMap mW,
-                                                              const __grid_constant__ CUtensorMap mS,
-                                                              const __grid_constant__ CUtensorMap mO) {
-    constexpr int L = R1 * TP, NB = R1 / TP, XB = (L + TP) * 8, BOX = xbox(L), NBOX = L / BOX;
+// x pass + update with TMA: boxes {8, 1, BOX (x), 1} of 8 columns. MODE 0:
+// Cahn-Hilliard, 1: Allen-Cahn, 2: preconditioner only (S' = F_x^-1 (dt / (1 +
+// dt M0 kappa |k|^4) F_x W), S not read; the variable-mobility model's spectral step).
+// Two tile buffers, (L + TP) x 8 each, receive W and S by TMA. SEP (L = 1024):
+// a third buffer of the same size takes the transposes and stages the result,
+// and each field's next tile is loaded as soon as the current one is in
+// registers (one 256-thread CTA per SM). Otherwise each tile buffer, once read,
+// is that FFT's transpose space and the S buffer stages the result. The next W
+// is then loaded after the W transposes, the next S once the store has read the
+// staging tile (the next tile's W phase covers that load). Without the third
+// buffer, three CTAs fit on an SM for L <= 512 and L = 400.
+template <int R1, int TP, int MODE, bool SEP>
+__global__ void __launch_bounds__(8 * TP, SEP ? 1 : (8 * TP >= 128 ? 3 : 1))
+    fxupd_tma_kernel(XUpdArgs a, int ntiles, const __grid_constant__ CUtensorMap mW,
+                     const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mO) {
+    constexpr int P = 8, L = R1 * TP, NB = R1 / TP, XB = (L + TP) * P, BOX = xbox(L), NBOX = L / BOX, NT = P * TP;
     static_assert(L % BOX == 0 && BOX <= 256, "x-pass TMA box");
     extern __shared__ __align__(1024) float4 smem4[];
-    float2* bufW = reinterpret_cast<float2*>(smem4);
-    float2* bufS = bufW + L * 8;
-    float2* xb = bufS + L * 8;
-    float2* tA = xb + XB;                                    // [L] twiddles (n2 ownership)
-    float2* tB = tA + L;                                     // [L] twiddles (block ownership)
-    float* k2xs = reinterpret_cast<float*>(tB + L);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(k2xs + L);  // [0] W, [1] S
-    const int p = threadIdx.x & 7, n2 = threadIdx.x >> 3;
+    float2* bufW = reinterpret_cast<float2*>(smem4);  // [XB] W tile (then its transposes unless SEP)
+    float2* bufS = bufW + XB;                          // [XB] S tile (then transposes and staging unless SEP)
+    float2* xb = bufS + XB;                            // [XB] transposes and staging (SEP only)
+    float2* tA = SEP ? xb + XB : xb;                   // [L] twiddles (n2 ownership)
+    float2* tB = NB == 1 ? tA : tA + L;                // [L] block ownership (the same table when TP = R1)
+    float* k2xs = reinterpret_cast<float*>(tA + (NB == 1 ? L : 2 * L));  // [L] |k_x|^2 (SEP only)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(k2xs + (SEP ? L : 0));  // [0] W, [1] S
+    const float* k2x = SEP ? k2xs : a.k2x;             // read through L1 otherwise
+    float2* const xW = SEP ? xb : bufW;                // transpose space of F_x W
+    float2* const xS = SEP ? xb : bufS;                // of F_x S, F_x^-1 and the store staging
+    const int p = threadIdx.x % P, n2 = threadIdx.x / P;
     const int nchunks = a.nchunks;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    fill_twiddles<R1, TP>(tA, tB, a.tw, 8 * TP);
-    for (int i = threadIdx.x; i < L; i += 8 * TP) k2xs[i] = a.k2x[i];
+    fill_twiddles<R1, TP>(tA, tB, a.tw, NT);
+    if (SEP)
+        for (int i = threadIdx.x; i < L; i += NT) k2xs[i] = a.k2x[i];
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
         mbar_init(bars + 0, 1);
@@ -685,10 +696,10 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
     auto issue = [&](const CUtensorMap* m, float2* buf, uint64_t* bar, int tl) {
         const int ky = tl / nchunks, chunk = tl - ky * nchunks;
         fence_async_smem();
-        mbar_expect_tx(bar, L * 8 * sizeof(float2));
+        mbar_expect_tx(bar, L * P * sizeof(float2));
 #pragma unroll
         for (int b = 0; b < NBOX; ++b)
-            tma_load4(buf + b * BOX * 8, m, chunk * 8, ky % YB, b * BOX, ky / YB, bar);
+            tma_load4(buf + b * BOX * P, m, chunk * P, ky % YB, b * BOX, ky / YB, bar);
     };
     constexpr bool AC = MODE == 1, PRE = MODE == 2;
     if (threadIdx.x == 0) {
@@ -704,15 +715,19 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         mbar_wait_or_abort(bars + 0, parity, &s_abort);
         float2 v[R1];
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[n1] = bufW[(n2 + TP * n1) * 8 + p];
-        if (threadIdx.x == 0) bulk_wait_read0();
-        __syncthreads();
-        if (threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
+        for (int n1 = 0; n1 < R1; ++n1) v[n1] = bufW[(n2 + TP * n1) * P + p];
+        if (SEP && threadIdx.x == 0) bulk_wait_read0();  // the previous store has left xb
+        __syncthreads();  // W tile read
+        if (SEP && threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
         Dft<R1, -1>::run(v);
         twiddle_a<R1, TP, -1>(v, n2, tA);
-        t1_s<R1, TP, 8>(v, xb, n2, p);
+        t1_s<R1, TP, P>(v, xW, n2, p);
         pass_b<R1, TP, -1>(v);
-        const int kz = chunk * 8 + p;
+        if (!SEP) {
+            __syncthreads();  // transpose reads done: bufW takes the next tile's W
+            if (threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
+        }
+        const int kz = chunk * P + p;
         const bool valid = kz < a.ncols;
         const float k2yz = a.k2y[ky] + (valid ? a.k2z[kz] : 0.f);
         float2 G[R1];
@@ -720,7 +735,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         for (int i = 0; i < NB; ++i)
 #pragma unroll
             for (int c = 0; c < TP; ++c) {
-                const float k2g = k2xs[n2 * NB + i + R1 * c] + k2yz;
+                const float k2g = (SEP ? k2x[n2 * NB + i + R1 * c] : __ldg(k2x + n2 * NB + i + R1 * c)) + k2yz;
                 const float f = PRE  ? a.dtM * a.invL * rcp_approx(fmaf(a.dtMk, k2g * k2g, 1.f))
                                 : AC ? ndtM
                                      : ndtM * k2g;
@@ -735,12 +750,12 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
             mbar_wait_or_abort(bars + 1, parity, &s_abort);
             parity ^= 1;
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) v[n1] = bufS[(n2 + TP * n1) * 8 + p];
-            __syncthreads();
-            if (threadIdx.x == 0 && next < ntiles) issue(&mS, bufS, bars + 1, next);
+            for (int n1 = 0; n1 < R1; ++n1) v[n1] = bufS[(n2 + TP * n1) * P + p];
+            __syncthreads();  // S tile read (and, with SEP, the W transposes' reads of xb done)
+            if (SEP && threadIdx.x == 0 && next < ntiles) issue(&mS, bufS, bars + 1, next);
             Dft<R1, -1>::run(v);
             twiddle_a<R1, TP, -1>(v, n2, tA);
-            t1_s<R1, TP, 8>(v, xb, n2, p);
+            t1_s<R1, TP, P>(v, xS, n2, p);
             pass_b<R1, TP, -1>(v);
             // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L; k = 0 stays out
             //      (Allen-Cahn: (c_hat - dt L g_hat) / (1 + dt L kappa |k|^2) / L)
@@ -748,7 +763,7 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
             for (int i = 0; i < NB; ++i)
 #pragma unroll
                 for (int c = 0; c < TP; ++c) {
-                    const float k2 = k2xs[n2 * NB + i + R1 * c] + k2yz;
+                    const float k2 = (SEP ? k2x[n2 * NB + i + R1 * c] : __ldg(k2x + n2 * NB + i + R1 * c)) + k2yz;
                     const float f = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
                     v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), f);
                 }
@@ -757,19 +772,23 @@ __global__ void __launch_bounds__(8 * TP, 1) fxupd_tma_kernel(XUpdArgs a, int nt
         // ---- S' = F_x^-1 c_hat'
         pass_b<R1, TP, 1>(v);
         twiddle_b<R1, TP, 1>(v, n2, tB);
-        __syncthreads();
-        t2_s<R1, TP, 8>(v, xb, n2, p);
+        __syncthreads();  // earlier transpose reads of xS done
+        t2_s<R1, TP, P>(v, xS, n2, p);
         Dft<R1, 1>::run(v);
-        __syncthreads();  // transpose reads done: xb becomes the store staging tile
+        __syncthreads();  // transpose reads done: xS becomes the store staging tile
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) xb[(n2 + TP * n1) * 8 + p] = v[n1];
+        for (int n1 = 0; n1 < R1; ++n1) xS[(n2 + TP * n1) * P + p] = v[n1];
         fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int b = 0; b < NBOX; ++b)
-                tma_store4(&mO, chunk * 8, ky % YB, b * BOX, ky / YB, xb + b * BOX * 8);
+                tma_store4(&mO, chunk * P, ky % YB, b * BOX, ky / YB, xS + b * BOX * P);
             bulk_commit();
+            if (!SEP) {
+                bulk_wait_read0();  // the store has read the staging tile: bufS takes the next S
+                if (!PRE && next < ntiles) issue(&mS, bufS, bars + 1, next);
+            }
         }
     }
     if (threadIdx.x == 0) bulk_wait0();
@@ -838,14 +857,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 4D map of a y-blocked half-spectrum buffer: dims {ncols, YB, nx, ny / YB}
-// (complex64 as 8-byte elements), box {8, b1, b2, b3}
-static bool make_map(CUtensorMap* m, const void* base, int ncols, int YB, int nx, int ny, long long Zp, int b1,
-                     int b2, int b3) {
+// (complex64 as 8-byte elements), box {b0, b1, b2, b3} (b0 columns: 4 or 8, 32 or 64 bytes)
+static bool make_map(CUtensorMap* m, const void* base, int ncols, int YB, int nx, int ny, long long Zp, int b0,
+                     int b1, int b2, int b3) {
     auto fn = encode_fn();
     if (!fn || ((uintptr_t)base & 15) || (ny % YB)) return false;
     cuuint64_t dims[4] = {(cuuint64_t)ncols, (cuuint64_t)YB, (cuuint64_t)nx, (cuuint64_t)(ny / YB)};
     cuuint64_t strides[3] = {(cuuint64_t)(Zp * 8), (cuuint64_t)(YB * Zp * 8), (cuuint64_t)((long long)nx * YB * Zp * 8)};
-    cuuint32_t box[4] = {8, (cuuint32_t)b1, (cuuint32_t)b2, (cuuint32_t)b3};
+    cuuint32_t box[4] = {(cuuint32_t)b0, (cuuint32_t)b1, (cuuint32_t)b2, (cuuint32_t)b3};
     cuuint32_t es[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, const_cast<void*>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -871,8 +890,8 @@ static bool run_fspass_tma(const SPassArgs& a, cudaStream_t st, cudaError_t* err
     if (a.rs * a.YB != a.os || a.YB > 256 || BOX % a.YB || BOX / a.YB > 256) return false;
     const long long Zp = a.rs;
     CUtensorMap mi, mo;
-    if (!make_map(&mi, a.in, a.ncols, a.YB, a.nouter, a.L, Zp, a.YB, 1, BOX / a.YB) ||
-        !make_map(&mo, a.out, a.ncols, a.YB, a.nouter, a.L, Zp, a.YB, 1, BOX / a.YB))
+    if (!make_map(&mi, a.in, a.ncols, a.YB, a.nouter, a.L, Zp, 8, a.YB, 1, BOX / a.YB) ||
+        !make_map(&mo, a.out, a.ncols, a.YB, a.nouter, a.L, Zp, 8, a.YB, 1, BOX / a.YB))
         return false;
     const size_t smem = sizeof(float2) * (L * 8 + (L + TP) * 8 + 2 * L) + 16;
     int per = 0;
@@ -891,19 +910,22 @@ static bool run_fspass_tma(const SPassArgs& a, cudaStream_t st, cudaError_t* err
 template <int R1, int TP>
 static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) {
     constexpr int L = R1 * TP, BOX = fast::xbox(L);
+    constexpr bool SEP = L == 1024;  // separate transpose/staging buffer (see fxupd_tma_kernel)
     // x pass geometry: rows x (rs = YB Zp), lines y split in blocks of YB (os = Zp)
     if (a.os * a.YB != a.rs) return false;
     const long long Zp = a.os;
     CUtensorMap mw, ms, mo;
-    if (!make_map(&mw, a.W, a.ncols, a.YB, a.L, a.ny, Zp, 1, BOX, 1) ||
-        !make_map(&ms, a.S, a.ncols, a.YB, a.L, a.ny, Zp, 1, BOX, 1) ||
-        !make_map(&mo, a.S_out, a.ncols, a.YB, a.L, a.ny, Zp, 1, BOX, 1))
+    if (!make_map(&mw, a.W, a.ncols, a.YB, a.L, a.ny, Zp, 8, 1, BOX, 1) ||
+        !make_map(&ms, a.S, a.ncols, a.YB, a.L, a.ny, Zp, 8, 1, BOX, 1) ||
+        !make_map(&mo, a.S_out, a.ncols, a.YB, a.L, a.ny, Zp, 8, 1, BOX, 1))
         return false;
-    const size_t smem = sizeof(float2) * (2 * L * 8 + (L + TP) * 8 + 2 * L) + sizeof(float) * L + 16;
+    const size_t smem =
+        sizeof(float2) * ((SEP ? 3 : 2) * (size_t)(L + TP) * 8 + (R1 == TP ? 1 : 2) * (size_t)L) +
+        (SEP ? sizeof(float) * L : 0) + 16;
     int per = 0;
-    auto kern = a.model == 2   ? fast::fxupd_tma_kernel<R1, TP, 2>
-                : a.model == 1 ? fast::fxupd_tma_kernel<R1, TP, 1>
-                               : fast::fxupd_tma_kernel<R1, TP, 0>;
+    auto kern = a.model == 2   ? fast::fxupd_tma_kernel<R1, TP, 2, SEP>
+                : a.model == 1 ? fast::fxupd_tma_kernel<R1, TP, 1, SEP>
+                               : fast::fxupd_tma_kernel<R1, TP, 0, SEP>;
     cudaError_t e = prep(kern, smem, 8 * TP, &per);
     if (e != cudaSuccess) {
         *err = e;

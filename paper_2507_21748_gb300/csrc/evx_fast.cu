@@ -666,6 +666,7 @@ __global__ void __launch_bounds__(8 * TP, SEP ? 1 : (8 * TP >= 128 ? 3 : 1))
     fxupd_tma_kernel(XUpdArgs a, int ntiles, const __grid_constant__ CUtensorMap mW,
                      const __grid_constant__ CUtensorMap mS, const __grid_constant__ CUtensorMap mO) {
     constexpr int P = 8, L = R1 * TP, NB = R1 / TP, XB = (L + TP) * P, BOX = xbox(L), NBOX = L / BOX, NT = P * TP;
+    constexpr int FWD_UNROLL = SEP ? 1 : 2;  // see the forward loop below
     static_assert(L % BOX == 0 && BOX <= 256, "x-pass TMA box");
     extern __shared__ __align__(1024) float4 smem4[];
     float2* bufW = reinterpret_cast<float2*>(smem4);  // [XB] W tile (then its transposes unless SEP)
@@ -711,62 +712,57 @@ __global__ void __launch_bounds__(8 * TP, SEP ? 1 : (8 * TP >= 128 ? 3 : 1))
     for (; tile < ntiles; tile += gridDim.x) {
         const int ky = tile / nchunks, chunk = tile - ky * nchunks;
         const int next = tile + gridDim.x;
-        // ---- g_hat = F_x W, kept as G = -dt M |k|^2 g_hat (Allen-Cahn: -dt L g_hat)
-        mbar_wait_or_abort(bars + 0, parity, &s_abort);
-        float2 v[R1];
-#pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[n1] = bufW[(n2 + TP * n1) * P + p];
-        if (SEP && threadIdx.x == 0) bulk_wait_read0();  // the previous store has left xb
-        __syncthreads();  // W tile read
-        if (SEP && threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
-        Dft<R1, -1>::run(v);
-        twiddle_a<R1, TP, -1>(v, n2, tA);
-        t1_s<R1, TP, P>(v, xW, n2, p);
-        pass_b<R1, TP, -1>(v);
-        if (!SEP) {
-            __syncthreads();  // transpose reads done: bufW takes the next tile's W
-            if (threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
-        }
+        // ---- f = 0: g_hat = F_x W, kept as G = -dt M |k|^2 g_hat (Allen-Cahn: -dt L g_hat);
+        //      f = 1: c_hat = F_x S and the update. With SEP (L = 1024) the loop is not
+        //      unrolled: both fields run through one copy of the forward FFT, which cut the
+        //      instruction-fetch stalls of this large kernel (x pass 3.15 -> 3.04 ms at 1024^3).
         const int kz = chunk * P + p;
         const bool valid = kz < a.ncols;
         const float k2yz = a.k2y[ky] + (valid ? a.k2z[kz] : 0.f);
-        float2 G[R1];
+        float2 v[R1], G[R1];
+#pragma unroll FWD_UNROLL
+        for (int f = 0; f < (PRE ? 1 : 2); ++f) {
+            float2* const buf = f ? bufS : bufW;
+            mbar_wait_or_abort(bars + f, parity, &s_abort);
 #pragma unroll
-        for (int i = 0; i < NB; ++i)
-#pragma unroll
-            for (int c = 0; c < TP; ++c) {
-                const float k2g = (SEP ? k2x[n2 * NB + i + R1 * c] : __ldg(k2x + n2 * NB + i + R1 * c)) + k2yz;
-                const float f = PRE  ? a.dtM * a.invL * rcp_approx(fmaf(a.dtMk, k2g * k2g, 1.f))
-                                : AC ? ndtM
-                                     : ndtM * k2g;
-                G[i * TP + c] = cscale(v[i * TP + c], f);
-            }
-        if (PRE) {
-            parity ^= 1;
-#pragma unroll
-            for (int q = 0; q < R1; ++q) v[q] = G[q];
-        } else {
-            // ---- c_hat = F_x S
-            mbar_wait_or_abort(bars + 1, parity, &s_abort);
-            parity ^= 1;
-#pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) v[n1] = bufS[(n2 + TP * n1) * P + p];
-            __syncthreads();  // S tile read (and, with SEP, the W transposes' reads of xb done)
-            if (SEP && threadIdx.x == 0 && next < ntiles) issue(&mS, bufS, bars + 1, next);
+            for (int n1 = 0; n1 < R1; ++n1) v[n1] = buf[(n2 + TP * n1) * P + p];
+            if (SEP && f == 0 && threadIdx.x == 0) bulk_wait_read0();
+            __syncthreads();
+            if (SEP && threadIdx.x == 0 && next < ntiles) issue(f ? &mS : &mW, buf, bars + f, next);
             Dft<R1, -1>::run(v);
             twiddle_a<R1, TP, -1>(v, n2, tA);
-            t1_s<R1, TP, P>(v, xS, n2, p);
+            t1_s<R1, TP, P>(v, f ? xS : xW, n2, p);
             pass_b<R1, TP, -1>(v);
-            // ---- c_hat' = (c_hat - dt M |k|^2 g_hat) / (1 + dt M kappa |k|^4) / L; k = 0 stays out
-            //      (Allen-Cahn: (c_hat - dt L g_hat) / (1 + dt L kappa |k|^2) / L)
-#pragma unroll
-            for (int i = 0; i < NB; ++i)
-#pragma unroll
-                for (int c = 0; c < TP; ++c) {
-                    const float k2 = (SEP ? k2x[n2 * NB + i + R1 * c] : __ldg(k2x + n2 * NB + i + R1 * c)) + k2yz;
-                    const float f = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
-                    v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), f);
+            if (f == 0) {
+                if (!SEP) {
+                    __syncthreads();
+                    if (threadIdx.x == 0 && next < ntiles) issue(&mW, bufW, bars + 0, next);
                 }
+#pragma unroll
+                for (int i = 0; i < NB; ++i)
+#pragma unroll
+                    for (int c = 0; c < TP; ++c) {
+                        const float k2g = (SEP ? k2x[n2 * NB + i + R1 * c] : __ldg(k2x + n2 * NB + i + R1 * c)) + k2yz;
+                        const float fa = PRE  ? a.dtM * a.invL * rcp_approx(fmaf(a.dtMk, k2g * k2g, 1.f))
+                                         : AC ? ndtM
+                                              : ndtM * k2g;
+                        G[i * TP + c] = cscale(v[i * TP + c], fa);
+                    }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NB; ++i)
+#pragma unroll
+                    for (int c = 0; c < TP; ++c) {
+                        const float k2 = (SEP ? k2x[n2 * NB + i + R1 * c] : __ldg(k2x + n2 * NB + i + R1 * c)) + k2yz;
+                        const float fa = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
+                        v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), fa);
+                    }
+            }
+        }
+        parity ^= 1;
+        if (PRE) {
+#pragma unroll
+            for (int q = 0; q < R1; ++q) v[q] = G[q];
         }
         if (ky == 0 && kz == 0 && n2 == 0) v[0] = make_float2(0.f, 0.f);
         // ---- S' = F_x^-1 c_hat'

@@ -31,7 +31,11 @@
  *   - Work is issued on the grid's CUDA stream and is asynchronous unless the
  *     entry point says it synchronises.
  *   - Sizes: nx, ny, nz each even, 8 <= n <= 1024, with no prime factor other
- *     than 2, 3 and 5; otherwise EVX_ERR_SIZE.
+ *     than 2, 3 and 5; otherwise EVX_ERR_SIZE. Every such size runs the same
+ *     arithmetic. Each pass picks its kernel by its own length: nx, ny in
+ *     {64, ..., 1024 powers of two, 400} and nz in {128, ..., 1024 powers of
+ *     two, 400} take the tuned four-step kernels; other lengths take the
+ *     mixed-radix ones (same results to FP32 rounding, several times slower).
  */
 #ifndef EVX_H
 #define EVX_H

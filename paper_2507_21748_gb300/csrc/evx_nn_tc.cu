@@ -684,7 +684,7 @@ cudaError_t launch_ring(const ConvArgs& a, cudaStream_t st, int sms, bool* launc
     const long long ncol = (long long)a.B * a.X * r.nzc;
     int nseg = 1;  // split columns along y until there are enough units for an even spread
     while (ncol * nseg < 8LL * sms && nseg * 2 <= a.Y / 8) nseg *= 2;
-    if (ncol * nseg > (1LL << 30)) return cudaSuccess;
+    if (ncol * nseg > (1LL << 30)) return cudaSuccess;  // unit index would overflow int: not launched, tile kernel
     r.nseg = nseg;
     r.nunits = (int)(ncol * nseg);
     cudaError_t e = cudaFuncSetAttribute(conv_ring_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, ring::SMEM);

@@ -55,7 +55,8 @@ typedef enum {
     EVX_ERR_OOM = 3,       /* device allocation failed */
     EVX_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed */
     EVX_ERR_NONFINITE = 5, /* a reduction found NaN or Inf in the field */
-    EVX_ERR_STATE = 6      /* call made in the wrong state (e.g. no field set) */
+    EVX_ERR_STATE = 6,     /* call made in the wrong state (e.g. no field set) */
+    EVX_ERR_IO = 7         /* checkpoint file cannot be opened, read or written, or is corrupt */
 } evx_status;
 
 /* Scheme parameters: time step dt, mobility M (>= 0), gradient coefficient
@@ -72,7 +73,11 @@ typedef struct {
  * Zp = roundup(nz/2 + 1, 8)), FP64 scalars, reduction scratch and the
  * twiddle and wave-number tables. cuda_stream: a cudaStream_t (NULL = the
  * legacy default stream). *out receives the handle. The grid holds no field
- * until evx_set_field. */
+ * until evx_set_field. On EVX_ERR_OOM every buffer the call allocated has been
+ * freed. Test hook for the allocation-failure paths (host side, no GPU fault):
+ * with EVX_FAIL_ALLOC=k in the environment, the k-th and every later device
+ * allocation within one call (evx_grid_create, evx_set_model, evx_ch_adjoint)
+ * reports failure without calling cudaMalloc. */
 evx_status evx_grid_create(int nx, int ny, int nz, evx_params p, void *cuda_stream,
                            evx_grid **out);
 
@@ -83,6 +88,9 @@ evx_status evx_grid_destroy(evx_grid *g);
 /* Replace dt, M, kappa, h (validated as above). Takes effect for work issued
  * after the call. */
 evx_status evx_set_params(evx_grid *g, evx_params p);
+
+/* Current parameters of g (after evx_load: the checkpoint's). */
+evx_status evx_get_params(const evx_grid *g, evx_params *p);
 
 /* Change the stream later work is issued on (the caller orders it against
  * earlier work). */
@@ -208,15 +216,41 @@ evx_status evx_pass_bytes(const evx_grid *g, int pass, double *bytes);
  * in one static device array of 8 MiB that every GPU loading the library
  * holds until the process exits; grids above 64^3 = 262144 voxels return
  * EVX_ERR_SIZE (size rules otherwise as above). No cudaMalloc/cudaFree or
- * allocating library call is made. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and should happen before any
- * stream capture. Work is issued asynchronously on cuda_stream. Every call
+ * allocating library call is made. It always runs the Cahn-Hilliard model, on
+ * the mixed-radix kernels (they have no bounded waits, so a call leaves no
+ * device-side flag to report). The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture begins. Work is issued asynchronously on cuda_stream. Every call
  * shares the array (its contents persist between calls; the call clears what
  * must start at zero), so calls that overlap on the GPU - e.g. on two streams
  * - race and must be serialised by the caller. Errors: EVX_ERR_ARG,
  * EVX_ERR_SIZE, EVX_ERR_CUDA; message via evx_last_error(NULL). */
 evx_status evx_ch_step_static(const float *d_c_in, float *d_c_out, int nx, int ny, int nz,
                               evx_params p, int n_steps, void *cuda_stream);
+
+/* Steps taken since the field was last set (evx_set_field*, evx_load restores
+ * the saved count, evx_ch_adjoint leaves n_steps). Host output. */
+evx_status evx_step_count(const evx_grid *g, long long *steps);
+
+/* Checkpoint and resume of a run. The paper has no checkpoint format of its
+ * own; this serves long runs of the scheme above (subsection "Semi-implicit
+ * timestepping") that must survive a restart.
+ * evx_save synchronises the grid's stream and writes to the file at path: a
+ * header (magic "EVXCKPT1", version 1, nx, ny, nz, model, y block and row pitch
+ * of the state layout, dt, M, kappa, h, the FP64 mean, the step count, the
+ * payload size and its FNV-1a 64-bit checksum) followed by the state buffer as
+ * the grid holds it (the half-spectrum state S of the spectral models, or the
+ * real FP32 field of EVX_MODEL_VM). evx_load reads such a file into a grid of
+ * the same size, model and layout, restores the parameters, the FP64 mean and
+ * the step count, and synchronises; stepping on from it gives bit-for-bit the
+ * fields of an uninterrupted run. The payload is read and checked before the
+ * grid's state changes. Errors: EVX_ERR_ARG (NULL), EVX_ERR_STATE (no field to
+ * save; size, model or layout mismatch), EVX_ERR_IO (open, read, write,
+ * truncated or checksum mismatch), EVX_ERR_CUDA. The host buffer used is
+ * allocated and freed inside the call (the state's size, or 64 MiB chunks on
+ * save). */
+evx_status evx_save(evx_grid *g, const char *path);
+evx_status evx_load(evx_grid *g, const char *path);
 
 /* Last error message of g (or of the calling thread when g is NULL). */
 const char *evx_last_error(const evx_grid *g);

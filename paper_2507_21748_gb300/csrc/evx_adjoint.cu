@@ -231,12 +231,9 @@ static evx_status adj_alloc(evx_grid* g, int K, int nseg) {
     const size_t fspec = (size_t)g->nx * g->ny * g->Zp * sizeof(float2);
     const size_t freal = (size_t)g->nx * g->ny * g->nz * sizeof(float);
     const int xg = (g->Zp / SP) * g->ny;
+    begin_alloc_call(g);
     auto get = [&](void** p, size_t b) -> bool {
-        if (cudaMalloc(p, b) != cudaSuccess) {
-            cudaGetLastError();
-            *p = nullptr;
-            return false;
-        }
+        if (!device_alloc(g, p, b)) return false;
         s->bytes += b;
         return true;
     };

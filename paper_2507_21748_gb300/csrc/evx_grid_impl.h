@@ -36,6 +36,8 @@ struct evx_grid {
     long long pass_cnt[4] = {0, 0, 0, 0};
     size_t bytes = 0;
     AdjStore* adj = nullptr;
+    long long steps = 0;         // steps taken since the field was set (saved by evx_save)
+    int call_allocs = 0;         // device allocations made in the current public call
 };
 
 
@@ -45,5 +47,11 @@ evx::XUpdArgs x_args(const evx_grid* g, const float2* W, float2* S, float2* S_ou
                      double M, double kappa);
 evx::ZPassArgs z_args(const evx_grid* g);
 evx_status set_error(evx_grid* g, evx_status s, const char* msg);
+// Every device allocation a grid makes goes through device_alloc. Test hook
+// (host-side fault injection): when the environment sets EVX_FAIL_ALLOC=k
+// (k >= 1), the k-th and every later allocation of one public call report
+// failure without calling cudaMalloc. begin_alloc_call starts the count.
+void begin_alloc_call(evx_grid* g);
+bool device_alloc(evx_grid* g, void** p, size_t bytes);
 void adjoint_free(evx_grid* g);  // evx_adjoint.cu
 }  // namespace evxrt

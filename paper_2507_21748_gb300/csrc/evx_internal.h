@@ -37,6 +37,7 @@ struct SPassArgs {
     int nchunks;        // column chunks of P
     Plan plan;
     const float2* tw;   // L-entry table exp(-2 pi i m / L)
+    int generic;        // 1: mixed-radix kernel only (no fast path, no bounded waits)
 };
 
 // x pass fused with the k-space update (one step of the scheme).
@@ -60,6 +61,7 @@ struct XUpdArgs {
                         // 1 Allen-Cahn:    b = -dt L,       D = 1 + dt L kappa |k|^2
                         // 2 preconditioner: S_out = F_x^-1 dt / (1 + dtMk |k|^4) F_x W / L,
                         //   S not read (dtM holds dt)
+    int generic;        // 1: mixed-radix kernel only (no fast path, no bounded waits)
 };
 
 // Energy: gradient term sum_k w(kz) |k|^2 |c_hat|^2 from the state S.
@@ -104,6 +106,7 @@ struct ZPassArgs {
     // map_rows = 1: real rows rin / rout are a caller's C-order field; memory
     // row r of the y-blocked spectrum is caller row x * ny + y
     int map_rows, YB, nxr, nyr;
+    int generic;            // 1: mixed-radix kernel only (no fast path)
 };
 __host__ __device__ inline long long user_row(long long r, int YB, int nx, int ny) {
     const long long x = (r / YB) % nx, yb = r / ((long long)YB * nx), yi = r % YB;

@@ -483,7 +483,7 @@ bool fast_paths_enabled() {
 
 cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st) {
     cudaError_t fe;
-    if (fast_paths_enabled() && fast_spass(a, dir, st, &fe)) return fe;
+    if (!a.generic && fast_paths_enabled() && fast_spass(a, dir, st, &fe)) return fe;
     const size_t sm = spass_smem(a.L);
     dim3 grid(a.nchunks, a.nouter);
     cudaError_t e;
@@ -499,7 +499,7 @@ cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st) {
 
 cudaError_t launch_xupdate(const XUpdArgs& a, cudaStream_t st) {
     cudaError_t fe;
-    if (fast_paths_enabled() && fast_xupdate(a, st, &fe)) return fe;
+    if (!a.generic && fast_paths_enabled() && fast_xupdate(a, st, &fe)) return fe;
     const size_t sm = xupdate_smem(a.L);
     cudaError_t e;
     if ((e = set_smem(xupdate_kernel, sm)) != cudaSuccess) return e;
@@ -523,8 +523,8 @@ int zpass_grid(const ZPassArgs& a) {
 
 cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st, int* grid_used) {
     cudaError_t fe;
-    if (mode == Z_STEP && fast_paths_enabled() && fast_zstep(a, st, &fe, grid_used)) return fe;
-    if ((mode == Z_R2C || mode == Z_C2R) && a.fast_ok && fast_paths_enabled() &&
+    if (mode == Z_STEP && !a.generic && fast_paths_enabled() && fast_zstep(a, st, &fe, grid_used)) return fe;
+    if ((mode == Z_R2C || mode == Z_C2R) && a.fast_ok && !a.generic && fast_paths_enabled() &&
         fast_zconv(a, mode == Z_R2C ? -1 : 1, st, &fe, grid_used))
         return fe;
     const size_t sm = zpass_smem(a.M, a.PZ, a.rows_per_cta);

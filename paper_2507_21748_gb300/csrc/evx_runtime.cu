@@ -4,11 +4,13 @@
 #include <cstdint>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "evx_grid_impl.h"
+#include "evx_tables.h"
 
 using namespace evx;
 
@@ -33,40 +35,10 @@ static evx_status fail(evx_grid* g, evx_status s, const char* fmt, ...) {
             return fail(g, EVX_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-static bool smooth235(int n) {
-    for (int p : {2, 3, 5})
-        while (n % p == 0) n /= p;
-    return n == 1;
-}
-
-static Plan make_plan(int L) {
-    Plan pl{};
-    int n = L;
-    while (n % 5 == 0) { pl.r[pl.n++] = 5; n /= 5; }
-    while (n % 3 == 0) { pl.r[pl.n++] = 3; n /= 3; }
-    while (n % 16 == 0) { pl.r[pl.n++] = 16; n /= 16; }
-    if (n == 8 || n == 4 || n == 2) { pl.r[pl.n++] = n; n = 1; }
-    return pl;
-}
-
-static std::vector<float2> twiddles(int L) {
-    std::vector<float2> t(L);
-    for (int m = 0; m < L; ++m) {
-        const double ang = -2.0 * M_PI * (double)m / (double)L;
-        t[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    }
-    return t;
-}
-
-static std::vector<float> k2table(int n, double h, int count) {
-    std::vector<float> t(count);
-    for (int m = 0; m < count; ++m) {
-        const int ms = m <= n / 2 ? m : m - n;
-        const double k = 2.0 * M_PI * (double)ms / ((double)n * h);
-        t[m] = (float)(k * k);
-    }
-    return t;
-}
+using evxrt::k2table;
+using evxrt::make_plan;
+using evxrt::smooth235;
+using evxrt::twiddles;
 
 static evx_status check_params(evx_grid* g, const evx_params& p) {
     if (!(p.dt >= 0) || !(p.M >= 0) || !(p.kappa >= 0) || !(p.h > 0) || !std::isfinite(p.dt) ||
@@ -82,14 +54,30 @@ static void drop_graphs(evx_grid* g) {
     g->g1 = g->gN = nullptr;
 }
 
+namespace evxrt {
+void begin_alloc_call(evx_grid* g) { g->call_allocs = 0; }
+
+bool device_alloc(evx_grid* g, void** p, size_t bytes) {
+    *p = nullptr;
+    const int k = ++g->call_allocs;
+    if (const char* env = std::getenv("EVX_FAIL_ALLOC")) {
+        const int at = std::atoi(env);
+        if (at >= 1 && k >= at) return false;  // injected failure: cudaMalloc is not called
+    }
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
+}  // namespace evxrt
+
 template <typename T>
 static evx_status dmalloc(evx_grid* g, T** ptr, size_t bytes) {
-    cudaError_t e = cudaMalloc((void**)ptr, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *ptr = nullptr;
-        return fail(g, EVX_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-    }
+    if (!evxrt::device_alloc(g, (void**)ptr, bytes))
+        return fail(g, EVX_ERR_OOM, "device allocation of %zu bytes failed (allocation %d of the call)", bytes,
+                    g->call_allocs);
     g->bytes += bytes;
     return EVX_OK;
 }
@@ -316,6 +304,7 @@ evx_status evx_grid_create(int nx, int ny, int nz, evx_params p, void* cuda_stre
     }
     if (check_params(nullptr, p) != EVX_OK) return EVX_ERR_ARG;
     g = new evx_grid();
+    evxrt::begin_alloc_call(g);
     g->nx = nx;
     g->ny = ny;
     g->nz = nz;
@@ -349,14 +338,7 @@ evx_status evx_grid_create(int nx, int ny, int nz, evx_params p, void* cuda_stre
         TRY(upload(g, &g->twx, twiddles(nx)));
         TRY(upload(g, &g->twy, twiddles(ny)));
         TRY(upload(g, &g->twz, twiddles(g->M)));
-        {
-            std::vector<float2> r(g->M + 1);
-            for (int k = 0; k <= g->M; ++k) {
-                const double ang = -2.0 * M_PI * (double)k / (double)nz;
-                r[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-            }
-            TRY(upload(g, &g->rtw, r));
-        }
+        TRY(upload(g, &g->rtw, twiddles(nz, g->M + 1)));  // exp(-2 pi i k / nz), k <= M
         TRY(dmalloc(g, &g->k2x, sizeof(float) * nx));
         TRY(dmalloc(g, &g->k2y, sizeof(float) * ny));
         TRY(dmalloc(g, &g->k2z, sizeof(float) * (g->M + 1)));
@@ -405,6 +387,12 @@ evx_status evx_set_params(evx_grid* g, evx_params p) {
     return EVX_OK;
 }
 
+evx_status evx_get_params(const evx_grid* g, evx_params* p) {
+    if (!g || !p) return fail(nullptr, EVX_ERR_ARG, "NULL argument");
+    *p = g->p;
+    return EVX_OK;
+}
+
 evx_status evx_set_stream(evx_grid* g, void* cuda_stream) {
     if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
     g->st = (cudaStream_t)cuda_stream;
@@ -432,6 +420,7 @@ static evx_status load_real(evx_grid* g, const float* rows, long long pitch, int
     // x pass with a = 1, b = 0: removes the k = 0 mode (carried in FP64)
     CK(launch_xupdate(x_args(g, nullptr, g->W, g->S, 0.0, 0.0, 0.0), g->st));
     g->has_field = true;
+    g->steps = 0;
     return EVX_OK;
 }
 
@@ -443,6 +432,7 @@ evx_status evx_set_field(evx_grid* g, const float* d_c) {
     if (g->model == EVX_MODEL_VM) {  // the variable-mobility state is the real field itself
         CK(cudaMemcpyAsync(g->S, d_c, field_bytes(g), cudaMemcpyDeviceToDevice, g->st));
         g->has_field = true;
+        g->steps = 0;
         return EVX_OK;
     }
     return load_real(g, d_c, g->nz, 1);
@@ -474,6 +464,7 @@ evx_status evx_set_field_host(evx_grid* g, const float* h_c) {
         CK(cudaMemcpyAsync(g->S, h_c, field_bytes(g), cudaMemcpyHostToDevice, g->st));
         CK(cudaStreamSynchronize(g->st));
         g->has_field = true;
+        g->steps = 0;
         return EVX_OK;
     }
     // one contiguous copy into S's memory (the state is rebuilt from it: the R2C
@@ -539,12 +530,9 @@ evx_status evx_set_model(evx_grid* g, int model) {
         CK(cudaStreamSynchronize(g->st));
         drop_graphs(g);
         if (model == EVX_MODEL_VM && !g->R) {
-            if (cudaMalloc(&g->R, field_bytes(g)) != cudaSuccess) {
-                cudaGetLastError();
-                g->R = nullptr;
-                return fail(g, EVX_ERR_OOM, "out of device memory for the right-hand-side buffer");
-            }
-            g->bytes += field_bytes(g);
+            evxrt::begin_alloc_call(g);
+            evx_status s = dmalloc(g, &g->R, field_bytes(g));
+            if (s != EVX_OK) return s;
         }
         // CH and AC share the spectral state; the variable-mobility state is the real field
         if (model == EVX_MODEL_VM || g->model == EVX_MODEL_VM) g->has_field = false;
@@ -566,6 +554,7 @@ evx_status evx_step(evx_grid* g, int n_steps) {
     if (n_steps < 0) return fail(g, EVX_ERR_ARG, "n_steps < 0");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     if (n_steps == 0) return EVX_OK;
+    g->steps += n_steps;
     if (g->prof) {
         for (int i = 0; i < n_steps; ++i) {
             if ((size_t)g->ev_used + 5 > g->evpool.size()) {
@@ -720,6 +709,141 @@ evx_status evx_pass_bytes(const evx_grid* g, int pass, double* bytes) {
     const double F = (double)g->nx * g->ny * (g->M + 1) * sizeof(float2);
     // pass 0 reads W and S, writes S; passes 1..3 read one field and write one
     *bytes = pass == 0 ? 3.0 * F : 2.0 * F;
+    return EVX_OK;
+}
+
+evx_status evx_step_count(const evx_grid* g, long long* steps) {
+    if (!g || !steps) return fail(nullptr, EVX_ERR_ARG, "NULL argument");
+    *steps = g->steps;
+    return EVX_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------ checkpoint / resume
+// File: a fixed header, then the payload (the state buffer exactly as the grid
+// holds it), little-endian as both host architectures store it.
+namespace {
+struct CkptHeader {
+    char magic[8];              // "EVXCKPT1"
+    uint32_t version, header_bytes;
+    int32_t nx, ny, nz, model, YB, Zp;
+    double dt, M, kappa, h;
+    double cbar;                // FP64 mean (the k = 0 mode)
+    int64_t steps;
+    uint64_t payload_bytes, payload_fnv;
+};
+const char CKPT_MAGIC[8] = {'E', 'V', 'X', 'C', 'K', 'P', 'T', '1'};
+constexpr size_t CKPT_CHUNK = 64u << 20;  // host staging per copy
+
+uint64_t fnv1a(uint64_t h, const unsigned char* p, size_t n) {
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ULL;
+    }
+    return h;
+}
+
+// the state buffer and its size: the spectral state (CH, AC) or the real field (VM)
+size_t state_bytes(const evx_grid* g) {
+    return g->model == EVX_MODEL_VM ? sizeof(float) * (size_t)g->nx * g->ny * g->nz
+                                    : sizeof(float2) * (size_t)g->nx * g->ny * g->Zp;
+}
+}  // namespace
+
+extern "C" {
+
+evx_status evx_save(evx_grid* g, const char* path) {
+    if (!g || !path) return fail(g, EVX_ERR_ARG, "NULL argument");
+    if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    CK(cudaStreamSynchronize(g->st));
+    evx_status s = check_timeouts(g);
+    if (s != EVX_OK) return s;
+    CkptHeader hd{};
+    std::memcpy(hd.magic, CKPT_MAGIC, 8);
+    hd.version = 1;
+    hd.header_bytes = sizeof(CkptHeader);
+    hd.nx = g->nx;
+    hd.ny = g->ny;
+    hd.nz = g->nz;
+    hd.model = g->model;
+    hd.YB = g->YB;
+    hd.Zp = g->Zp;
+    hd.dt = g->p.dt;
+    hd.M = g->p.M;
+    hd.kappa = g->p.kappa;
+    hd.h = g->p.h;
+    hd.steps = g->steps;
+    if (g->model != EVX_MODEL_VM) CK(cudaMemcpy(&hd.cbar, g->d_scal, sizeof(double), cudaMemcpyDeviceToHost));
+    const size_t total = state_bytes(g);
+    hd.payload_bytes = total;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(g, EVX_ERR_IO, "cannot open %s for writing", path);
+    std::vector<unsigned char> buf(std::min(total, CKPT_CHUNK));
+    bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1;
+    uint64_t h = 0xcbf29ce484222325ULL;
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(g->S);
+    for (size_t off = 0; ok && off < total; off += buf.size()) {
+        const size_t n = std::min(buf.size(), total - off);
+        if (cudaMemcpy(buf.data(), src + off, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(f);
+            return fail(g, EVX_ERR_CUDA, "state copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        h = fnv1a(h, buf.data(), n);
+        ok = std::fwrite(buf.data(), 1, n, f) == n;
+    }
+    hd.payload_fnv = h;  // the checksum goes into the header once the payload is written
+    ok = ok && std::fseek(f, 0, SEEK_SET) == 0 && std::fwrite(&hd, sizeof hd, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(g, EVX_ERR_IO, "write to %s failed", path);
+    return EVX_OK;
+}
+
+evx_status evx_load(evx_grid* g, const char* path) {
+    if (!g || !path) return fail(g, EVX_ERR_ARG, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(g, EVX_ERR_IO, "cannot open %s", path);
+    CkptHeader hd{};
+    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, CKPT_MAGIC, 8) != 0 || hd.version != 1 ||
+        hd.header_bytes != sizeof(CkptHeader)) {
+        std::fclose(f);
+        return fail(g, EVX_ERR_IO, "%s is not an evx checkpoint", path);
+    }
+    if (hd.nx != g->nx || hd.ny != g->ny || hd.nz != g->nz) {
+        std::fclose(f);
+        return fail(g, EVX_ERR_STATE, "checkpoint grid %d x %d x %d differs from this grid %d x %d x %d", hd.nx,
+                    hd.ny, hd.nz, g->nx, g->ny, g->nz);
+    }
+    if (hd.model != g->model) {
+        std::fclose(f);
+        return fail(g, EVX_ERR_STATE, "checkpoint holds model %d, the grid is set to model %d (evx_set_model first)",
+                    hd.model, g->model);
+    }
+    if (hd.YB != g->YB || hd.Zp != g->Zp || hd.payload_bytes != state_bytes(g)) {
+        std::fclose(f);
+        return fail(g, EVX_ERR_STATE, "checkpoint layout (y block %d, row pitch %d) differs from this grid's (%d, %d)",
+                    hd.YB, hd.Zp, g->YB, g->Zp);
+    }
+    const evx_params p{hd.dt, hd.M, hd.kappa, hd.h};
+    if (check_params(g, p) != EVX_OK) {
+        std::fclose(f);
+        return EVX_ERR_IO;
+    }
+    // read and verify the whole payload before the grid's state is touched
+    const size_t total = hd.payload_bytes;
+    std::vector<unsigned char> data(total);
+    const bool rd = std::fread(data.data(), 1, total, f) == total;
+    std::fclose(f);
+    if (!rd) return fail(g, EVX_ERR_IO, "%s is truncated", path);
+    if (fnv1a(0xcbf29ce484222325ULL, data.data(), total) != hd.payload_fnv)
+        return fail(g, EVX_ERR_IO, "%s: payload checksum mismatch", path);
+    evx_status s = evx_set_params(g, p);
+    if (s != EVX_OK) return s;
+    CK(cudaStreamSynchronize(g->st));
+    CK(cudaMemcpy(g->S, data.data(), total, cudaMemcpyHostToDevice));
+    if (g->model != EVX_MODEL_VM) CK(cudaMemcpy(g->d_scal, &hd.cbar, sizeof(double), cudaMemcpyHostToDevice));
+    g->has_field = true;
+    g->steps = hd.steps;
     return EVX_OK;
 }
 

@@ -6,13 +6,16 @@
 // work buffer, the FP64 scalars and reduction partials, the twiddle and
 // wave-number tables - lives in one file-scope static device array whose size
 // is fixed at compile time; the caller passes only the input and output
-// fields.
+// fields. The path runs the mixed-radix kernels in the plain [x][y][kz]
+// layout: they have no bounded waits, so nothing is left on the device for a
+// later call to report.
 #include <cmath>
 #include <cstdint>
 #include <mutex>
 #include <vector>
 
 #include "evx_grid_impl.h"
+#include "evx_tables.h"
 
 using namespace evx;
 
@@ -51,22 +54,6 @@ evx_status static_address(void** out) {
     return EVX_OK;
 }
 
-bool smooth235s(int n) {
-    for (int p : {2, 3, 5})
-        while (n % p == 0) n /= p;
-    return n == 1;
-}
-
-Plan plan_of(int L) {
-    Plan pl{};
-    int n = L;
-    while (n % 5 == 0) { pl.r[pl.n++] = 5; n /= 5; }
-    while (n % 3 == 0) { pl.r[pl.n++] = 3; n /= 3; }
-    while (n % 16 == 0) { pl.r[pl.n++] = 16; n /= 16; }
-    if (n == 8 || n == 4 || n == 2) { pl.r[pl.n++] = n; n = 1; }
-    return pl;
-}
-
 // bump allocator over the static array (256-byte aligned pieces)
 struct Carve {
     unsigned char* base;
@@ -81,6 +68,23 @@ struct Carve {
 };
 
 }  // namespace
+
+// pass arguments of the static path: always the mixed-radix kernels
+static SPassArgs ys(const evx_grid* g, const float2* in, float2* out) {
+    SPassArgs a = evxrt::y_args(g, in, out);
+    a.generic = 1;
+    return a;
+}
+static XUpdArgs xs(const evx_grid* g, const float2* W, float2* S, float2* S_out, double dt, double M, double kappa) {
+    XUpdArgs a = evxrt::x_args(g, W, S, S_out, dt, M, kappa);
+    a.generic = 1;
+    return a;
+}
+static ZPassArgs zs(const evx_grid* g) {
+    ZPassArgs a = evxrt::z_args(g);
+    a.generic = 1;
+    return a;
+}
 
 #define CKS(call)                                                                              \
     do {                                                                                       \
@@ -99,7 +103,7 @@ extern "C" evx_status evx_ch_step_static(const float* d_c_in, float* d_c_out, in
         !std::isfinite(p.M) || !std::isfinite(p.kappa) || !std::isfinite(p.h))
         return static_fail(EVX_ERR_ARG, "invalid parameters");
     for (int n : {nx, ny, nz})
-        if (n < 8 || n > 1024 || (n & 1) || !smooth235s(n))
+        if (n < 8 || n > 1024 || (n & 1) || !evxrt::smooth235(n))
             return static_fail(EVX_ERR_SIZE, "each edge must be even, 8..1024, prime factors 2, 3, 5");
     const long long V = (long long)nx * ny * nz;
     if (V > STATIC_MAX_VOXELS)
@@ -115,15 +119,17 @@ extern "C" evx_status evx_ch_step_static(const float* d_c_in, float* d_c_out, in
     g.ny = ny;
     g.nz = nz;
     g.M = nz / 2;
-    g.YB = choose_yblock(ny, fast_paths_enabled());
+    // plain [x][y][kz] layout and the mixed-radix kernels only: they have no
+    // bounded waits, so a call has no device-side timeout flag left to report
+    g.YB = choose_yblock(ny, false);
     g.Zp = ((g.M + 1 + SP - 1) / SP) * SP;
     g.PZ = (g.M + 2) & ~1;
     g.zrows = std::max(1, TILE_CAP / g.PZ);
     g.p = p;
     g.st = (cudaStream_t)cuda_stream;
-    g.px = plan_of(nx);
-    g.py = plan_of(ny);
-    g.pz = plan_of(g.M);
+    g.px = evxrt::make_plan(nx);
+    g.py = evxrt::make_plan(ny);
+    g.pz = evxrt::make_plan(g.M);
     const size_t nspec = (size_t)nx * ny * g.Zp;
     Carve cv{reinterpret_cast<unsigned char*>(addr)};
     g.S = cv.take<float2>(nspec);
@@ -144,31 +150,12 @@ extern "C" evx_status evx_ch_step_static(const float* d_c_in, float* d_c_out, in
     g.k2z = cv.take<float>(g.M + 1);
     if (cv.off > STATIC_BYTES) return static_fail(EVX_ERR_SIZE, "grid does not fit the static scratch");
 
-    // tables (host FP64, rounded to FP32), copied into the static array
-    auto tw = [](int L) {
-        std::vector<float2> t(L);
-        for (int m = 0; m < L; ++m) {
-            const double a = -2.0 * M_PI * (double)m / (double)L;
-            t[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
-        return t;
-    };
-    auto k2 = [&](int n, int count) {
-        std::vector<float> t(count);
-        for (int m = 0; m < count; ++m) {
-            const int ms = m <= n / 2 ? m : m - n;
-            const double k = 2.0 * M_PI * (double)ms / ((double)n * p.h);
-            t[m] = (float)(k * k);
-        }
-        return t;
-    };
-    std::vector<float2> r(g.M + 1);
-    for (int k = 0; k <= g.M; ++k) {
-        const double a = -2.0 * M_PI * (double)k / (double)nz;
-        r[k] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    const std::vector<float2> tx = tw(nx), ty = tw(ny), tz = tw(g.M);
-    const std::vector<float> kx = k2(nx, nx), ky = k2(ny, ny), kz = k2(nz, g.M + 1);
+    // tables (host FP64, rounded to FP32; the same functions as the grid path),
+    // copied into the static array
+    const std::vector<float2> tx = evxrt::twiddles(nx), ty = evxrt::twiddles(ny), tz = evxrt::twiddles(g.M),
+                              r = evxrt::twiddles(nz, g.M + 1);
+    const std::vector<float> kx = evxrt::k2table(nx, p.h, nx), ky = evxrt::k2table(ny, p.h, ny),
+                             kz = evxrt::k2table(nz, p.h, g.M + 1);
     cudaStream_t st = g.st;
     // pageable sources: each copy has read its host buffer when the call returns
     CKS(cudaMemcpyAsync(g.twx, tx.data(), sizeof(float2) * nx, cudaMemcpyHostToDevice, st));
@@ -186,31 +173,31 @@ extern "C" evx_status evx_ch_step_static(const float* d_c_in, float* d_c_out, in
     CKS(launch_sum_field(d_c_in, nrows, nz, nz, g.d_part, SUM_BLOCKS, st));
     CKS(launch_reduce_partials(g.d_part, SUM_BLOCKS, g.d_scal, 1.0 / (double)V, st));
     {
-        ZPassArgs z = evxrt::z_args(&g);
+        ZPassArgs z = zs(&g);
         z.rin = d_c_in;
         z.rpitch = nz;
         z.map_rows = 1;
         z.out = g.W;
         z.cbar = g.d_scal;
         CKS(launch_zpass(z, Z_R2C, st));
-        CKS(launch_spass(evxrt::y_args(&g, g.W, g.W), -1, st));
-        CKS(launch_xupdate(evxrt::x_args(&g, nullptr, g.W, g.S, 0.0, 0.0, 0.0), st));
+        CKS(launch_spass(ys(&g, g.W, g.W), -1, st));
+        CKS(launch_xupdate(xs(&g, nullptr, g.W, g.S, 0.0, 0.0, 0.0), st));
     }
     // n_steps semi-implicit steps
     for (int i = 0; i < n_steps; ++i) {
-        CKS(launch_spass(evxrt::y_args(&g, g.S, g.W), +1, st));
-        ZPassArgs z = evxrt::z_args(&g);
+        CKS(launch_spass(ys(&g, g.S, g.W), +1, st));
+        ZPassArgs z = zs(&g);
         z.in = g.W;
         z.out = g.W;
         z.cbar = g.d_scal;
         CKS(launch_zpass(z, Z_STEP, st));
-        CKS(launch_spass(evxrt::y_args(&g, g.W, g.W), -1, st));
-        CKS(launch_xupdate(evxrt::x_args(&g, g.W, g.S, g.S, p.dt, p.M, p.kappa), st));
+        CKS(launch_spass(ys(&g, g.W, g.W), -1, st));
+        CKS(launch_xupdate(xs(&g, g.W, g.S, g.S, p.dt, p.M, p.kappa), st));
     }
     // state -> output field
-    CKS(launch_spass(evxrt::y_args(&g, g.S, g.W), +1, st));
+    CKS(launch_spass(ys(&g, g.S, g.W), +1, st));
     {
-        ZPassArgs z = evxrt::z_args(&g);
+        ZPassArgs z = zs(&g);
         z.in = g.W;
         z.rout = d_c_out;
         z.rpitch = nz;

@@ -13,16 +13,18 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libevx.so")
 
-EVX_OK, EVX_ERR_ARG, EVX_ERR_SIZE, EVX_ERR_OOM, EVX_ERR_CUDA, EVX_ERR_NONFINITE, EVX_ERR_STATE = range(7)
+(EVX_OK, EVX_ERR_ARG, EVX_ERR_SIZE, EVX_ERR_OOM, EVX_ERR_CUDA, EVX_ERR_NONFINITE, EVX_ERR_STATE,
+ EVX_ERR_IO) = range(8)
 STATUS_NAMES = ["EVX_OK", "EVX_ERR_ARG", "EVX_ERR_SIZE", "EVX_ERR_OOM", "EVX_ERR_CUDA",
-                "EVX_ERR_NONFINITE", "EVX_ERR_STATE"]
+                "EVX_ERR_NONFINITE", "EVX_ERR_STATE", "EVX_ERR_IO"]
 
 # every entry point declared in include/evx.h
 EXPORTS = [
-    "evx_grid_create", "evx_grid_destroy", "evx_set_params", "evx_set_stream", "evx_set_field",
+    "evx_grid_create", "evx_grid_destroy", "evx_set_params", "evx_get_params", "evx_set_stream", "evx_set_field",
     "evx_set_field_host", "evx_get_field", "evx_get_field_host", "evx_ch_step", "evx_energy",
     "evx_mean", "evx_ch_adjoint", "evx_footprint", "evx_set_profiling", "evx_pass_times",
-    "evx_pass_bytes", "evx_ch_step_static", "evx_set_model", "evx_get_model", "evx_step", "evx_last_error",
+    "evx_pass_bytes", "evx_ch_step_static", "evx_set_model", "evx_get_model", "evx_step", "evx_step_count",
+    "evx_save", "evx_load", "evx_last_error",
 ]
 MODELS = {"ch": 0, "ac": 1, "vm": 2}  # evx_model: Cahn-Hilliard, Allen-Cahn, variable-mobility CH
 
@@ -49,6 +51,7 @@ def _load():
         "evx_grid_create": ([i, i, i, Params, vp, ctypes.POINTER(vp)], st),
         "evx_grid_destroy": ([vp], st),
         "evx_set_params": ([vp, Params], st),
+        "evx_get_params": ([vp, ctypes.POINTER(Params)], st),
         "evx_set_stream": ([vp, vp], st),
         "evx_set_field": ([vp, fp], st),
         "evx_set_field_host": ([vp, fp], st),
@@ -66,6 +69,9 @@ def _load():
         "evx_set_model": ([vp, i], st),
         "evx_get_model": ([vp], ctypes.c_int),
         "evx_step": ([vp, i], st),
+        "evx_step_count": ([vp, ctypes.POINTER(ctypes.c_longlong)], st),
+        "evx_save": ([vp, ctypes.c_char_p], st),
+        "evx_load": ([vp, ctypes.c_char_p], st),
         "evx_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -173,6 +179,23 @@ class Grid:
 
     def step(self, n=1):
         self._ck(lib.evx_step(self._h, int(n)))
+
+    @property
+    def steps(self):
+        n = ctypes.c_longlong()
+        self._ck(lib.evx_step_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def save(self, path):
+        """Write a checkpoint (state, FP64 mean, parameters, step count) to path."""
+        self._ck(lib.evx_save(self._h, os.fsencode(str(path))))
+
+    def load(self, path):
+        """Resume from a checkpoint written by save() for a grid of this size and model."""
+        self._ck(lib.evx_load(self._h, os.fsencode(str(path))))
+        p = Params()  # the checkpoint carries its parameters
+        self._ck(lib.evx_get_params(self._h, ctypes.byref(p)))
+        self.params = p
 
     def energy(self):
         E = ctypes.c_double()

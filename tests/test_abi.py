@@ -100,3 +100,17 @@ def test_model_and_engine_entry_points_reject_bad_arguments(lib):
     one = ctypes.c_void_p(16)  # never dereferenced: the size check comes first
     assert lib.evx_nn_conv3d(one, one, None, one, None, None, 1, 1, 3, 64, 32, 32, 0, None) == 2  # Y odd
     assert lib.evx_nn_conv3d(one, one, None, one, None, None, 1, 1, 2, 48, 32, 32, 0, None) == 2  # Z % 64
+
+
+def test_checkpoint_and_query_entry_points_reject_null(lib):
+    """evx_save / evx_load / evx_step_count / evx_get_params validate their
+    arguments on the host before touching a grid or a file."""
+    vp = ctypes.c_void_p
+    lib.evx_save.argtypes = [vp, ctypes.c_char_p]
+    lib.evx_load.argtypes = [vp, ctypes.c_char_p]
+    lib.evx_step_count.argtypes = [vp, vp]
+    lib.evx_get_params.argtypes = [vp, vp]
+    assert lib.evx_save(None, b"/nonexistent/x") == 1
+    assert lib.evx_load(None, b"/nonexistent/x") == 1
+    assert lib.evx_step_count(None, None) == 1
+    assert lib.evx_get_params(None, None) == 1

@@ -47,14 +47,17 @@ def test_dc_independent_of_kappa_and_exact_mass():
         assert abs(O.mass(out) - m0) / l1 < 1e-13
 
 
+@pytest.mark.parametrize("h", [1.0, 0.8])
 @pytest.mark.parametrize("mvec,A", [((3, 0, 0), 0.8), ((1, 2, 0), 0.5), ((2, 1, 1), 1.2)])
-def test_single_mode_closed_form(mvec, A):
+def test_single_mode_closed_form(mvec, A, h):
     """c = A cos(k1.x). Since cos^3 = (3 cos + cos 3)/4, g = (3A^3/4 - A) cos + (A^3/4) cos 3,
     so one step gives exactly alpha cos(k1.x) + beta cos(3 k1.x) with
     alpha = (A - dt M k1^2 (3A^3/4 - A)) / (1 + dt M kappa k1^4),
-    beta  = -dt M 9 k1^2 (A^3/4) / (1 + dt M kappa 81 k1^4)."""
+    beta  = -dt M 9 k1^2 (A^3/4) / (1 + dt M kappa 81 k1^4),
+    k1^2 = sum_d (2 pi m_d / (N h))^2. At h = 0.8 the wave numbers grow by 1/h,
+    which pins the voxel edge's scaling of the symbols."""
     N = 32
-    dt, M, kappa, h = 0.2, 0.9, 1.1, 1.0
+    dt, M, kappa = 0.2, 0.9, 1.1
     x = np.indices((N, N, N)).astype(np.float64)
     theta = 2 * np.pi * sum(mvec[d] * x[d] for d in range(3)) / N
     c = A * np.cos(theta)
@@ -120,17 +123,22 @@ def test_energy_monotone(offset):
     assert E[-1] < E[0]
 
 
-def test_energy_closed_form_single_mode():
-    """E of A cos(k.x): bulk h^3 sum (c^2-1)^2/4 and gradient (kappa/2) k^2 A^2 V/2."""
-    N, A, m = 16, 0.4, 3
-    x = np.arange(N)
-    c = np.broadcast_to((A * np.cos(2 * np.pi * m * x / N))[:, None, None], (N, N, N))
-    V = N ** 3
-    k2 = (2 * np.pi * m / N) ** 2
-    # mean of cos^2 = 1/2, cos^4 = 3/8 over full periods:
-    bulk = V * (A ** 4 * 3 / 8 - 2 * A ** 2 / 2 + 1) / 4
-    grad = 0.5 * 1.5 * k2 * A ** 2 * V / 2
-    assert abs(O.energy(c, 1.5) - (bulk + grad)) < 1e-10 * (bulk + grad)
+@pytest.mark.parametrize("h", [1.0, 0.8])
+@pytest.mark.parametrize("m", [(3, 0, 0), (1, 2, 3)])
+def test_energy_closed_form_single_mode(m, h):
+    """E of A cos(k.x) on an n-grid of edge h: the bulk term is h^3 sum (c^2-1)^2/4 =
+    h^3 V (3A^4/8 - A^2 + 1)/4 (means of cos^2 and cos^4 over whole periods: 1/2, 3/8),
+    and the gradient term h^3 (kappa/2) sum |grad c|^2 = h^3 (kappa/2) |k|^2 A^2 V/2 with
+    |k|^2 = sum_d (2 pi m_d / (n_d h))^2. At h = 0.8 the bulk term scales by h^3 and the
+    gradient term by h, which pins both factors."""
+    n, A, kappa = (16, 12, 20), 0.4, 1.5
+    X, Y, Z = np.meshgrid(*[np.arange(nd) for nd in n], indexing="ij")
+    c = A * np.cos(2 * np.pi * (m[0] * X / n[0] + m[1] * Y / n[1] + m[2] * Z / n[2]))
+    V = n[0] * n[1] * n[2]
+    k2 = sum((2 * np.pi * m[d] / (n[d] * h)) ** 2 for d in range(3))
+    bulk = h ** 3 * V * (A ** 4 * 3 / 8 - A ** 2 + 1) / 4
+    grad = h ** 3 * 0.5 * kappa * k2 * A ** 2 * V / 2
+    assert abs(O.energy(c, kappa, h) - (bulk + grad)) < 1e-10 * (bulk + grad)
 
 
 def test_first_order_in_dt():

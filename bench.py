@@ -136,8 +136,10 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling every 20 ms from before the warm-up steps to after the
+    timed region; the record reports the samples taken inside the timed region
+    (host wall-clock bracket) and, for context, all samples under load."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -152,12 +154,14 @@ class Clocks:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """t0, t1: time.time() bracket of the timed region (samples inside it are
+        the record; a sample is attributed to the 20 ms before its timestamp)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -165,24 +169,37 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sms, mx, reasons = [], None, set()
+        import datetime
+        rows, mx = [], None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sms.append(float(f[1]))
-                mx = float(f[2])
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm = float(f[2])
+                mx = float(f[3])
+                pw = float(f[4])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+            rows.append((ts, sm, pw, {nm for nm, v in zip(names, f[6:10]) if v.lower() == "active"}))
         os.unlink(self.path)
-        sms.sort()
-        med = sms[len(sms) // 2] if sms else None
-        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+        inside = [r for r in rows if t0 is not None and t0 <= r[0] <= t1 + 0.02]
+        loaded = [r for r in rows if r[2] > 300.0]  # under load (power draw above idle)
+
+        def med(xs):
+            xs = sorted(xs)
+            return xs[len(xs) // 2] if xs else None
+
+        rec = inside if inside else loaded
+        reasons = set()
+        for r in rec:
+            reasons |= r[3]
+        return {"sm_mhz": med([r[1] for r in rec]), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(inside), "interval_ms": 20,
+                "run_sm_mhz": med([r[1] for r in loaded]), "run_samples_under_load": len(loaded),
+                "run_reasons": sorted(set().union(*[r[3] for r in loaded])) if loaded else []}
 
 
 def cpu_baseline_oracle(n_sample=256, steps=2):
@@ -199,6 +216,47 @@ def cpu_baseline_oracle(n_sample=256, steps=2):
             "sample": "FP64 oracle (full complex 3D FFT, numpy + C/OpenMP), %d steps of the same "
                       "recipe on a %d^3 grid (%.1f s); its per-voxel cost grows with log V, so "
                       "at 1024^3 it would be no faster" % (steps, n_sample, dt)}
+
+
+def cpu_single_thread_oracle(n_sample=128, steps=1):
+    """The same oracle step on one host core (OMP_NUM_THREADS=1 in a child process,
+    since the OpenMP runtime reads it once at load)."""
+    code = ("import sys, time, json; sys.path.insert(0, %r)\n"
+            "from oracle import oracle as O\n"
+            "from paper_2507_21748_gb300 import inputs\n"
+            "c0 = inputs.uniform_field((%d,) * 3, seed=0, offset=0.3)\n"
+            "O.ch_step(c0[:8, :8, :8], %r, %r, %r, %r, 1)\n"
+            "t0 = time.perf_counter(); O.ch_step(c0, %r, %r, %r, %r, %d, check_imag=False)\n"
+            "print(json.dumps({'s': time.perf_counter() - t0, 'threads': O.num_threads()}))\n"
+            ) % (ROOT, n_sample, DT, MOB, KAPPA, H, DT, MOB, KAPPA, H, steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": steps * n_sample ** 3 / d["s"], "unit": UNIT, "cores": d["threads"], "kind": "oracle",
+            "sample": "same oracle, one thread, %d step(s) on a %d^3 grid (%.1f s)" % (steps, n_sample, d["s"])}
+
+
+def sampled_modes(n, count=14, seed=1):
+    """Wave vectors for the sampled-mode checks: fixed low, Nyquist and fastest-
+    growing modes plus random ones (k = 0 excluded; it is reported on its own)."""
+    rng = np.random.default_rng(seed)
+    fixed = np.array([[1, 0, 0], [0, 0, 1], [0, 0, n // 2], [n // 2, n // 2, n // 2], [114 * n // 1024, 0, 0],
+                      [3, 5, 7]])
+    return np.concatenate([fixed, rng.integers(0, n, size=(count - len(fixed), 3))])
+
+
+def mode_error(got_modes, want_modes, field_l2):
+    """Sampled-mode errors: the maximum |delta c_hat(k)| over the modes and the
+    estimate of the whole-field relative L2 it implies (by Parseval, the field's
+    rel. L2 error is the RMS of |delta c_hat| over all modes over ||c||_2)."""
+    d = np.abs(np.asarray(got_modes) - np.asarray(want_modes))
+    return {"modes": len(d), "max_abs_mode_err": float(d.max()),
+            "rel_l2_estimate": float(np.sqrt(np.mean(d * d)) / field_l2)}
+
+
+def field_l2(c):
+    return float(np.sqrt(sum(float(np.sum(np.asarray(c[i:i + 64], dtype=np.float64) ** 2))
+                             for i in range(0, c.shape[0], 64))))
 
 
 def bf16_peak():
@@ -307,12 +365,21 @@ def small_grid_bench():
     not bandwidth) and 256^3 / 400^3 (1000-step runs) with the same recipe as the
     parity tests (c0 = U(-0.05, 0.05), seed 0); CUDA-graph launches, CUDA events."""
     import torch
+    from oracle import oracle as O
     from paper_2507_21748_gb300 import evx, inputs
     out = {}
     for n, steps in ((64, 1000), (256, 1000), (400, 1000)):
         shape = (n, n, n)
+        c0 = inputs.uniform_field(shape, seed=0)
         g = evx.Grid(shape, dt=DT, M=MOB, kappa=KAPPA, h=H)
-        g.set_field(torch.from_numpy(inputs.uniform_field(shape, seed=0)).cuda())
+        # error after one step against the FP64 oracle, whole field (outside the timed region)
+        g.set_field(torch.from_numpy(c0).cuda())
+        g.step(1)
+        c1 = g.get_field().cpu().numpy().astype(np.float64)
+        ref = O.ch_step(c0, DT, MOB, KAPPA, H, 1, check_imag=False)
+        rel = float(np.linalg.norm(c1 - ref) / np.linalg.norm(ref))
+        del c1, ref
+        g.set_field(torch.from_numpy(c0).cuda())
         g.step(20)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -324,8 +391,11 @@ def small_grid_bench():
         out["%d^3" % n] = {"steps": steps, "us_per_step": 1e3 * ms / steps,
                            "voxel_steps_per_s": steps * float(n) ** 3 / (ms * 1e-3),
                            "footprint_bytes": g.footprint(),
-                           "kernels": "fast, L = 32 x TP" if n in (64, 128, 256, 512, 1024)
-                           else "fast, L = 20 x 20 (x, y), M = 200 = 20 x 10 (z)"}
+                           "kernels": ("fast, L = 32 x TP" if n in (64, 128, 256, 512, 1024)
+                                       else "fast, L = 20 x 20 (x, y), M = 200 = 20 x 10 (z)")
+                           + ("; fused y-z-y pass" if g.pass_bytes(2) == 0.0 else ""),
+                           "error_vs_oracle": {"rel_l2_one_step": rel, "what": "whole field, one step from "
+                                               "c0 = U(-0.05, 0.05) seed 0, FP64 oracle"}}
         g.close()
     return out
 
@@ -435,6 +505,8 @@ def main():
     c0_dev = torch.from_numpy(c0).cuda()
     stream = torch.cuda.current_stream()
     g = evx.Grid(shape, dt=DT, M=MOB, kappa=KAPPA, h=H, stream=stream)
+    clocks = Clocks(local)
+    clocks.start()
     g.set_field(c0_dev)
     g.step(max(args.warmup, 0))
     torch.cuda.synchronize()
@@ -446,18 +518,19 @@ def main():
     # ---- device-resident timed region (per-pass CUDA events on the grid's stream)
     g.set_profiling(True)
     g.pass_times(reset=True)
-    clocks = Clocks(local)
-    clocks.start()
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
     e0.record(stream)
     g.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    w1 = time.time()
     barrier()
-    clk = clocks.stop()
+    time.sleep(0.05)  # one more sample after the region
+    clk = clocks.stop(w0, w1)
     ms = e0.elapsed_time(e1)
     pass_ms, pass_cnt = g.pass_times(reset=True)
     g.set_profiling(False)
@@ -465,22 +538,48 @@ def main():
     value = job_throughput(ws, args.steps, V, t_max * 1e-3)
 
     # roofline of the dominant pass
+    fused = g.pass_bytes(2) == 0.0  # the y inverse, z step and y forward run as one fused pass
     names = ["x pass + k-space update", "y inverse", "z C2R + c^3-c + R2C", "y forward"]
+    if fused:
+        names = ["x pass + k-space update", "fused y inverse + z C2R/c^3-c/R2C + y forward (x slabs in L2)",
+                 "(in the fused pass)", "(in the fused pass)"]
     fast = n in (64, 128, 256, 512, 1024, 400) and os.environ.get("EVX_GENERIC", "") != "1"
     r1, tp = (20, 20) if n == 400 else (32, max(n // 32, 2))  # four-step split n = R1 x TP
     rz, tz, ntz = (20, 10, 160) if n == 400 else (32, max(tp // 2, 2), 128)  # z pass: M = n / 2
     kern = (["fast::fxupd_tma_kernel<%d, %d>" % (r1, tp), "fast::fspass_tma_kernel<%d, %d, 1>" % (r1, tp),
              "fast::fzstep_kernel<%d, %d, %d>" % (rz, tz, ntz), "fast::fspass_tma_kernel<%d, %d, -1>" % (r1, tp)]
             if fast else ["xupdate_kernel", "spass_kernel<1>", "zpass_kernel<Z_STEP>", "spass_kernel<-1>"])
+    if fused:
+        kern[1] = "fused::fyzy_kernel<%d, %d, %d, %d>" % (r1, tp, rz, tz)
+        kern[2] = kern[3] = "-"
     dom = max(range(4), key=lambda k: pass_ms[k])
     avg_ms = pass_ms[dom] / max(pass_cnt[dom], 1)
     alg_bytes = g.pass_bytes(dom)
     peak, peak_src = peaks()
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     step_bytes = sum(g.pass_bytes(k) for k in range(4))
-    per_pass = {names[k]: {"avg_ms": pass_ms[k] / max(pass_cnt[k], 1),
-                           "GBps": g.pass_bytes(k) / (pass_ms[k] / max(pass_cnt[k], 1) * 1e-3) / 1e9}
-                for k in range(4)}
+    field_bytes = g.pass_bytes(0) / 3.0  # F: one half-spectrum field, nx ny (nz/2 + 1) complex64
+    per_pass = {}
+    for k in range(4):
+        pm = pass_ms[k] / max(pass_cnt[k], 1)
+        per_pass[names[k] if k < 2 or not fused else names[k] + " %d" % k] = {
+            "kernel": kern[k], "avg_ms": pm, "alg_bytes": g.pass_bytes(k),
+            "GBps": g.pass_bytes(k) / (pm * 1e-3) / 1e9 if pm > 0 and g.pass_bytes(k) > 0 else None}
+
+    # ---- error of the timed configuration against the FP64 oracle (outside the timed region):
+    # one step from the bench's own input, sampled Fourier modes, each from the definition
+    from oracle import oracle as O
+    modes = sampled_modes(n)
+    g.set_field(c0_dev)
+    g.step(1)
+    c1 = g.get_field().cpu().numpy()
+    err_ch = mode_error(O.dft_modes(c1, modes, "c"), O.step_modes(c0, modes, DT, MOB, KAPPA, H), field_l2(c1))
+    err_ch["k0_rel_err"] = abs(float(np.sum(c1, dtype=np.float64)) - float(np.sum(c0, dtype=np.float64))) / \
+        abs(float(np.sum(c0, dtype=np.float64)))
+    err_ch["what"] = ("one step from the timed input; c_hat(k) of the GPU field vs the oracle's step evaluated "
+                      "mode by mode (direct FP64 sums, no FFT) at %d wave vectors incl. Nyquist and the fastest-"
+                      "growing mode; k = 0: FP64 sum of the FP32 field vs the input's" % len(modes))
+    del c1
 
     # ---- end to end through the host API
     e2e = None
@@ -519,7 +618,17 @@ def main():
         ac = {"workload": "Allen-Cahn %d^3, same c0, dt 0.1, L = kappa = 1, %d steps (after 3 warm-up)"
                           % (n, args.ac_steps),
               "value": job_throughput(ws, args.ac_steps, V, t_ac * 1e-3), "unit": UNIT,
-              "ms_per_step": t_ac / args.ac_steps, "launches_per_step": 5, "mean_after": g.mean()}
+              "ms_per_step": t_ac / args.ac_steps, "launches_per_step": 3 if fused else 5,
+              "mean_after": g.mean()}
+        g.set_field(c0_dev)
+        g.step(1)
+        c1 = g.get_field().cpu().numpy()
+        ac["error_vs_oracle"] = mode_error(O.dft_modes(c1, modes, "c"),
+                                           O.ac_step_modes(c0, modes, DT, MOB, KAPPA, H), field_l2(c1))
+        ac["error_vs_oracle"]["mean_abs_err"] = abs(g.mean() - float(np.real(O.ac_step_modes(
+            c0, np.zeros((1, 3), dtype=np.int64), DT, MOB, KAPPA, H)[0])) / V)
+        ac["error_vs_oracle"]["what"] = "one step, sampled modes as for the CH line; FP64 mean vs the oracle's"
+        del c1
         g.set_model("ch")
     # ---- variable-mobility Cahn-Hilliard (FD right-hand side, spectral preconditioner)
     vm = None
@@ -540,6 +649,14 @@ def main():
               "value": job_throughput(ws, args.vm_steps, V, t_vm * 1e-3), "unit": UNIT,
               "ms_per_step": t_vm / args.vm_steps, "launches_per_step": 7,
               "footprint_bytes": g.footprint()}
+        g.set_field(c0_dev)
+        g.step(1)
+        c1 = g.get_field().cpu().numpy()
+        vm["error_vs_oracle"] = mode_error(O.dft_modes(c1, modes, "c"),
+                                           O.vm_step_modes(c0, modes, DT, MOB, KAPPA, H), field_l2(c1))
+        vm["error_vs_oracle"]["what"] = ("one step, sampled modes; the oracle's FD right-hand side is formed "
+                                         "plane by plane and summed mode by mode")
+        del c1
         g.set_model("ch")
     g.close()
     del c0_dev
@@ -568,6 +685,10 @@ def main():
         except Exception as ex:  # report, do not fail the bench
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                    "sample": "failed: %r" % (ex,)}
+        try:
+            cpu["single_thread"] = cpu_single_thread_oracle()
+        except Exception as ex:  # report, do not fail the bench
+            cpu["single_thread"] = {"value": None, "sample": "failed: %r" % (ex,)}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -575,9 +696,13 @@ def main():
         "config": {"workload": "CH 3D periodic %d^3, c0 = 0.3 + U(-0.05,0.05) seed 0, dt 0.1, "
                                "M = kappa = 1, h = 1, %d steps" % (n, args.steps),
                    "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (%.2f GB per field vs 129 MB)" % (step_bytes / 9 / 1e9),
-                   "sweeps_per_step": 9,
+                   "l2": "inputs larger than L2 (%.2f GB per field vs 129 MB)" % (field_bytes / 1e9),
+                   "sweeps_per_step": step_bytes / field_bytes,
+                   "sweeps_note": ("x pass 3 (read W, S; write S) + fused y-z-y pass 2 (read S, write W; "
+                                   "the slab's intermediate sweeps stay in L2)" if fused else
+                                   "x pass 3 + y inverse 2 + z step 2 + y forward 2"),
                    "footprint_bytes": fp},
+        "error_vs_oracle": err_ch,
         "roofline": {"bound": "hbm", "kernel": kern[dom] + " (" + names[dom] + ")",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_src + " hbm_gbs (copy)",
@@ -590,7 +715,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": (2 if fused else 4) * args.steps,
         "allen_cahn": ac,
         "variable_mobility": vm,
         "small_grids": small,

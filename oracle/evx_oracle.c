@@ -18,6 +18,8 @@
  *                  (the pointwise chemical-potential term of the
  *                  Cahn-Hilliard right-hand side). Used to check single
  *                  Fourier modes of a large grid one by one.
+ *   orc_vm_rhs_modes  the same sums of the variable-mobility finite-
+ *                  difference right-hand side, formed plane by plane.
  *
  * Twiddle factors are evaluated with libm cos/sin in FP64.
  */
@@ -203,6 +205,125 @@ void orc_dft_modes(const float *c, int nx, int ny, int nz, int nmodes,
         }
         free(sy);
         free(sz);
+    }
+    for (int m = 0; m < nmodes; ++m) {
+        cplx s = 0;
+        for (int x = 0; x < nx; ++x) s += partial[(long)m * nx + x];
+        out_re[m] = creal(s);
+        out_im[m] = cimag(s);
+    }
+    free(partial);
+    free(ez);
+    free(ey);
+    free(ex);
+}
+
+/*
+ * Variable-mobility right-hand side on one x-plane and its Fourier modes.
+ * The general form of "Semi-implicit timestepping" with the mobility of Eq.
+ * (cahn-hilliard) read as M(c) = M max(1 - c^2, 0):
+ *   mu  = c^3 - c - kappa lap_h c,  lap_h the periodic 7-point Laplacian / h^2,
+ *   rhs = (1/h^2) sum_d [ (M_x + M_{x+e_d})/2 (mu_{x+e_d} - mu_x)
+ *                         - (M_{x-e_d} + M_x)/2 (mu_x - mu_{x-e_d}) ].
+ * orc_vm_rhs_modes returns the direct sums sum_x rhs(x) exp(-i k.x) at the
+ * given integer wave vectors. Each x-plane of rhs is formed on its own from
+ * the c planes x-2 .. x+2 (mu and M on planes x-1, x, x+1), then summed like
+ * orc_dft_modes; per-x partial sums are added in order.
+ */
+static long wrap(long i, long n) { return ((i % n) + n) % n; }
+
+static void vm_mu_plane(const float *c, int nx, int ny, int nz, long p, double kappa, double h, double *out)
+{
+    const long x = wrap(p, nx), xm = wrap(p - 1, nx), xp = wrap(p + 1, nx);
+    for (long y = 0; y < ny; ++y) {
+        const long ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
+        for (long z = 0; z < nz; ++z) {
+            const long zm = wrap(z - 1, nz), zp = wrap(z + 1, nz);
+            const double v = c[(x * ny + y) * nz + z];
+            const double lap = ((double)c[(xp * ny + y) * nz + z] + (double)c[(xm * ny + y) * nz + z]
+                                + (double)c[(x * ny + yp) * nz + z] + (double)c[(x * ny + ym) * nz + z]
+                                + (double)c[(x * ny + y) * nz + zp] + (double)c[(x * ny + y) * nz + zm]
+                                - 6.0 * v) / (h * h);
+            out[y * nz + z] = v * v * v - v - kappa * lap;
+        }
+    }
+}
+
+static void vm_mob_plane(const float *c, int nx, int ny, int nz, long p, double M, double *out)
+{
+    const long x = wrap(p, nx);
+    for (long i = 0; i < (long)ny * nz; ++i) {
+        const double v = c[x * ny * nz + i];
+        const double m = 1.0 - v * v;
+        out[i] = M * (m > 0.0 ? m : 0.0);
+    }
+}
+
+void orc_vm_rhs_modes(const float *c, int nx, int ny, int nz, double M, double kappa, double h,
+                      int nmodes, const int *modes, double *out_re, double *out_im)
+{
+    cplx *ex = (cplx *)malloc(sizeof(cplx) * (size_t)nmodes * nx);
+    cplx *ey = (cplx *)malloc(sizeof(cplx) * (size_t)nmodes * ny);
+    cplx *ez = (cplx *)malloc(sizeof(cplx) * (size_t)nmodes * nz);
+    for (int m = 0; m < nmodes; ++m) {
+        for (int x = 0; x < nx; ++x)
+            ex[(long)m * nx + x] = cexp(-I * TWO_PI * (double)(((long)modes[3 * m] * x) % nx) / nx);
+        for (int y = 0; y < ny; ++y)
+            ey[(long)m * ny + y] = cexp(-I * TWO_PI * (double)(((long)modes[3 * m + 1] * y) % ny) / ny);
+        for (int z = 0; z < nz; ++z)
+            ez[(long)m * nz + z] = cexp(-I * TWO_PI * (double)(((long)modes[3 * m + 2] * z) % nz) / nz);
+    }
+    cplx *partial = (cplx *)malloc(sizeof(cplx) * (size_t)nmodes * nx);
+    const long P = (long)ny * nz;
+#pragma omp parallel
+    {
+        double *mu = (double *)malloc(sizeof(double) * 3 * P);   /* planes x-1, x, x+1 */
+        double *mob = (double *)malloc(sizeof(double) * 3 * P);
+        double *rhs = (double *)malloc(sizeof(double) * P);
+        cplx *sz = (cplx *)malloc(sizeof(cplx) * (size_t)nmodes);
+        cplx *sy = (cplx *)malloc(sizeof(cplx) * (size_t)nmodes);
+#pragma omp for schedule(static)
+        for (int x = 0; x < nx; ++x) {
+            for (int j = 0; j < 3; ++j) {
+                vm_mu_plane(c, nx, ny, nz, x - 1 + j, kappa, h, mu + j * P);
+                vm_mob_plane(c, nx, ny, nz, x - 1 + j, M, mob + j * P);
+            }
+            const double *u0 = mu + P, *m0 = mob + P;
+            for (long y = 0; y < ny; ++y) {
+                const long ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
+                for (long z = 0; z < nz; ++z) {
+                    const long zm = wrap(z - 1, nz), zp = wrap(z + 1, nz);
+                    const long i = y * nz + z;
+                    /* neighbour indices within the three planes: -x, +x, -y, +y, -z, +z */
+                    const double un[6] = {mu[i], mu[2 * P + i], u0[ym * nz + z], u0[yp * nz + z], u0[y * nz + zm],
+                                          u0[y * nz + zp]};
+                    const double mn[6] = {mob[i], mob[2 * P + i], m0[ym * nz + z], m0[yp * nz + z], m0[y * nz + zm],
+                                          m0[y * nz + zp]};
+                    double acc = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double fp = 0.5 * (m0[i] + mn[2 * d + 1]) * (un[2 * d + 1] - u0[i]);
+                        const double fm = 0.5 * (mn[2 * d] + m0[i]) * (u0[i] - un[2 * d]);
+                        acc += fp - fm;
+                    }
+                    rhs[i] = acc / (h * h);
+                }
+            }
+            for (int m = 0; m < nmodes; ++m) sy[m] = 0;
+            for (long y = 0; y < ny; ++y) {
+                for (int m = 0; m < nmodes; ++m) sz[m] = 0;
+                for (long z = 0; z < nz; ++z) {
+                    const double f = rhs[y * nz + z];
+                    for (int m = 0; m < nmodes; ++m) sz[m] += f * ez[(long)m * nz + z];
+                }
+                for (int m = 0; m < nmodes; ++m) sy[m] += sz[m] * ey[(long)m * ny + y];
+            }
+            for (int m = 0; m < nmodes; ++m) partial[(long)m * nx + x] = sy[m] * ex[(long)m * nx + x];
+        }
+        free(sy);
+        free(sz);
+        free(rhs);
+        free(mob);
+        free(mu);
     }
     for (int m = 0; m < nmodes; ++m) {
         cplx s = 0;

@@ -83,6 +83,8 @@ def _L():
         lib.orc_fft3d.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_dft_modes.argtypes = [fp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ip, ctypes.c_int, dp, dp]
+        lib.orc_vm_rhs_modes.argtypes = [fp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ip, dp, dp]
         lib.orc_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -324,6 +326,47 @@ def step_modes(c32, modes, dt, M, kappa, h=1.0):
     ch = dft_modes(c32, md, "c")
     gh = dft_modes(c32, md, "g")
     return (ch - dt * M * k2 * gh) / (1.0 + dt * M * kappa * k2 * k2)
+
+
+def _mode_k2(shape, md, h):
+    k2 = np.zeros(md.shape[0])
+    for d in range(3):
+        k2 += wavenumbers(shape[d], h)[md[:, d] % shape[d]] ** 2
+    return k2
+
+
+def ac_step_modes(c32, modes, dt, L, kappa, h=1.0):
+    """Allen-Cahn c_hat^{n+1}(k) = (c_hat - dt L g_hat) / (1 + dt L kappa |k|^2) at
+    selected k after one step from c32, each mode from direct DFT sums."""
+    md = np.asarray(modes, dtype=np.int64).reshape(-1, 3)
+    k2 = _mode_k2(c32.shape, md, h)
+    ch = dft_modes(c32, md, "c")
+    gh = dft_modes(c32, md, "g")
+    return (ch - dt * L * gh) / (1.0 + dt * L * kappa * k2)
+
+
+def vm_rhs_modes(c32, modes, M, kappa, h=1.0):
+    """sum_x rhs(x) exp(-i k.x) of the variable-mobility FD right-hand side
+    (``vm_rhs``), formed plane by plane in C (no full-size FP64 arrays)."""
+    c32 = np.ascontiguousarray(c32, dtype=np.float32)
+    md = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, 3))
+    n = md.shape[0]
+    re = np.zeros(n)
+    im = np.zeros(n)
+    nx, ny, nz = c32.shape
+    _L().orc_vm_rhs_modes(c32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), nx, ny, nz, float(M), float(kappa),
+                          float(h), n, md.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                          re.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          im.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return re + 1j * im
+
+
+def vm_step_modes(c32, modes, dt, M, kappa, h=1.0):
+    """Variable-mobility c_hat^{n+1}(k) = c_hat + dt / (1 + dt M kappa |k|^4) rhs_hat
+    at selected k after one step from c32."""
+    md = np.asarray(modes, dtype=np.int64).reshape(-1, 3)
+    k2 = _mode_k2(c32.shape, md, h)
+    return dft_modes(c32, md, "c") + dt / (1.0 + dt * M * kappa * k2 * k2) * vm_rhs_modes(c32, md, M, kappa, h)
 
 
 # ---------------------------------------------------------------- adjoint

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libevx.so")
-SOURCES = ["evx_kernels.cu", "evx_fast.cu", "evx_runtime.cu", "evx_adjoint.cu", "evx_static.cu",
+SOURCES = ["evx_kernels.cu", "evx_fast.cu", "evx_fused.cu", "evx_runtime.cu", "evx_adjoint.cu", "evx_static.cu",
            "evx_nn.cu", "evx_nn_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

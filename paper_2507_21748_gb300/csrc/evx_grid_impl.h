@@ -36,6 +36,9 @@ struct evx_grid {
     long long pass_cnt[4] = {0, 0, 0, 0};
     size_t bytes = 0;
     AdjStore* adj = nullptr;
+    int* ctl = nullptr;          // fused y-z-y pass: ticket, abort word, per-slab counters
+    bool fused = false;          // the step runs the fused y-z-y pass (evx_fused.cu)
+    int lag = 3;                 // its slab lag
     long long steps = 0;         // steps taken since the field was set (saved by evx_save)
     int call_allocs = 0;         // device allocations made in the current public call
 };
@@ -46,6 +49,7 @@ evx::SPassArgs y_args(const evx_grid* g, const float2* in, float2* out);
 evx::XUpdArgs x_args(const evx_grid* g, const float2* W, float2* S, float2* S_out, double dt,
                      double M, double kappa);
 evx::ZPassArgs z_args(const evx_grid* g);
+evx::YZYArgs yzy_args(const evx_grid* g);
 evx_status set_error(evx_grid* g, evx_status s, const char* msg);
 // Every device allocation a grid makes goes through device_alloc. Test hook
 // (host-side fault injection): when the environment sets EVX_FAIL_ALLOC=k

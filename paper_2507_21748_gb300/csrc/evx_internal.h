@@ -113,6 +113,30 @@ __host__ __device__ inline long long user_row(long long r, int YB, int nx, int n
     return x * ny + yb * YB + yi;
 }
 
+// Fused y inverse + z step + y forward (evx_fused.cu): S (state, F_y F_z c)
+// -> W (F_y F_z (g(c) - g(cbar))), per x slab in L2 (see the file's header).
+struct YZYArgs {
+    const float2* S;
+    float2* W;
+    int nx, ny, Zp, YB;
+    long long os2;          // stride between y blocks (nx * YB * Zp)
+    int ncols, nchunks;     // valid columns (M + 1), column chunks of 8
+    const float2* twy;      // ny-entry table exp(-2 pi i m / ny)
+    const float2* twz;      // M-entry table
+    const float2* rtw;      // (M + 1)-entry table exp(-2 pi i k / nz)
+    float scale;            // 1 / (ny nz)
+    const double* cbar;     // FP64 mean
+    double* gsum;           // Allen-Cahn: per-CTA FP64 sums of g(c) - g(cbar), or null
+    int* ctl;               // fused_ctl_ints(nx) ints: ticket, abort word, per-slab counters (cleared per launch)
+    int lag;                // slabs between a slab's stages in the ticket order
+};
+int fused_yzy_shape(int ny, int M, int YB);  // 1 if a fused kernel exists for this y / z geometry
+bool fused_yzy_enabled();                    // false under EVX_NO_FUSE=1 or EVX_GENERIC=1
+size_t fused_ctl_ints(int nx);
+cudaError_t launch_fused_yzy(const YZYArgs& a, cudaStream_t st, int* grid_used);
+int fused_yzy_grid(const YZYArgs& a);        // CTAs a launch may use (partials it may write)
+bool fused_timeout_flag(int* flag, bool clear);
+
 // launchers (evx_kernels.cu)
 cudaError_t launch_spass(const SPassArgs& a, int dir, cudaStream_t st);
 cudaError_t launch_xupdate(const XUpdArgs& a, cudaStream_t st);

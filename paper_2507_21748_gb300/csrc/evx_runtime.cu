@@ -162,6 +162,27 @@ ZPassArgs z_args(const evx_grid* g) {
     return a;
 }
 
+YZYArgs yzy_args(const evx_grid* g) {
+    YZYArgs a{};
+    a.S = g->S;
+    a.W = g->W;
+    a.nx = g->nx;
+    a.ny = g->ny;
+    a.Zp = g->Zp;
+    a.YB = g->YB;
+    a.os2 = (long long)g->nx * g->YB * g->Zp;
+    a.ncols = g->M + 1;
+    a.nchunks = g->Zp / SP;
+    a.twy = g->twy;
+    a.twz = g->twz;
+    a.rtw = g->rtw;
+    a.scale = (float)(1.0 / ((double)g->ny * g->nz));
+    a.cbar = g->d_scal;
+    a.ctl = g->ctl;
+    a.lag = g->lag;
+    return a;
+}
+
 evx_status set_error(evx_grid* g, evx_status s, const char* msg) { return fail(g, s, "%s", msg); }
 
 }  // namespace evxrt
@@ -212,6 +233,28 @@ static cudaError_t issue_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) {
     if (g->model == EVX_MODEL_VM) return issue_vm_step(g, st, ev);
     cudaError_t e;
     if (ev) cudaEventRecord(ev[0], st);
+    if (g->fused) {  // y inverse + z step + y forward in one pass (its time is reported as pass 1)
+        YZYArgs y = yzy_args(g);
+        const bool ac = g->model == EVX_MODEL_AC;
+        if (ac) y.gsum = g->d_part;
+        int grid = 0;
+        if ((e = launch_fused_yzy(y, st, &grid)) != cudaSuccess) return e;
+        if (ac) {
+            const double V = (double)g->nx * g->ny * g->nz;
+            if (grid <= 0 || grid > g->npart) return cudaErrorInvalidValue;
+            if ((e = launch_ac_mean(g->d_part, grid, g->d_scal, g->p.dt * g->p.M, 1.0 / V, st)) != cudaSuccess)
+                return e;
+        }
+        if (ev) {
+            cudaEventRecord(ev[1], st);
+            cudaEventRecord(ev[2], st);
+            cudaEventRecord(ev[3], st);
+        }
+        if ((e = launch_xupdate(x_args(g, g->W, g->S, g->S, g->p.dt, g->p.M, g->p.kappa), st)) != cudaSuccess)
+            return e;
+        if (ev) cudaEventRecord(ev[4], st);
+        return cudaSuccess;
+    }
     if ((e = launch_spass(y_args(g, g->S, g->W), +1, st)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     ZPassArgs z = z_args(g);
@@ -262,6 +305,8 @@ static evx_status check_timeouts(evx_grid* g) {
     int f = 0;
     if (fast_timeout_flag(&f, true) && f)
         return fail(g, EVX_ERR_CUDA, "a bounded TMA wait timed out in a fast kernel; results are invalid");
+    if (fused_timeout_flag(&f, true) && f)
+        return fail(g, EVX_ERR_CUDA, "a bounded wait timed out in the fused y-z-y pass; results are invalid");
     return EVX_OK;
 }
 
@@ -334,6 +379,12 @@ evx_status evx_grid_create(int nx, int ny, int nz, evx_params p, void* cuda_stre
         const int zg = zpass_grid(z);
         const int xg = (g->Zp / SP) * ny;
         g->npart = std::max(std::max(zg, xg), SUM_BLOCKS);
+        if (fused_yzy_enabled() && fused_yzy_shape(ny, g->M, g->YB)) {
+            g->fused = true;
+            if (const char* lg = std::getenv("EVX_FUSE_LAG")) g->lag = std::min(16, std::max(1, std::atoi(lg)));
+            TRY(dmalloc(g, &g->ctl, sizeof(int) * fused_ctl_ints(nx)));
+            g->npart = std::max(g->npart, fused_yzy_grid(yzy_args(g)));
+        }
         TRY(dmalloc(g, &g->d_part, (size_t)g->npart * sizeof(double)));
         TRY(upload(g, &g->twx, twiddles(nx)));
         TRY(upload(g, &g->twy, twiddles(ny)));
@@ -364,7 +415,7 @@ evx_status evx_grid_destroy(evx_grid* g) {
     if (g->st || g->S) cudaStreamSynchronize(g->st);
     evxrt::adjoint_free(g);
     drop_graphs(g);
-    for (auto ptr : {(void*)g->S, (void*)g->W, (void*)g->R, (void*)g->d_scal, (void*)g->d_part, (void*)g->twx,
+    for (auto ptr : {(void*)g->S, (void*)g->W, (void*)g->R, (void*)g->ctl, (void*)g->d_scal, (void*)g->d_part, (void*)g->twx,
                      (void*)g->twy, (void*)g->twz, (void*)g->rtw, (void*)g->k2x, (void*)g->k2y,
                      (void*)g->k2z})
         if (ptr) cudaFree(ptr);
@@ -707,8 +758,13 @@ evx_status evx_pass_bytes(const evx_grid* g, int pass, double* bytes) {
     if (!g || !bytes || pass < 0 || pass > 3) return fail(nullptr, EVX_ERR_ARG, "bad argument");
     // one half-spectrum field: nx * ny * (M + 1) complex64 elements
     const double F = (double)g->nx * g->ny * (g->M + 1) * sizeof(float2);
-    // pass 0 reads W and S, writes S; passes 1..3 read one field and write one
-    *bytes = pass == 0 ? 3.0 * F : 2.0 * F;
+    // pass 0 reads W and S, writes S; passes 1..3 read one field and write one.
+    // With the fused y-z-y pass, pass 1 is that pass (read S, write W; the
+    // intermediate sweeps stay in L2) and passes 2 and 3 are empty.
+    if (g->fused && g->model != EVX_MODEL_VM)
+        *bytes = pass == 0 ? 3.0 * F : pass == 1 ? 2.0 * F : 0.0;
+    else
+        *bytes = pass == 0 ? 3.0 * F : 2.0 * F;
     return EVX_OK;
 }
 

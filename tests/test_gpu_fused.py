@@ -1,0 +1,130 @@
+"""The fused y-z-y pass (y inverse, z C2R -> c^3 - c -> z R2C and y forward in
+one persistent kernel whose x slabs stay in L2) against the three separate
+passes and the FP64 oracle, through the C-ABI.
+
+The separate passes run in a child process with EVX_NO_FUSE=1. The fused
+kernel applies the same transforms in the same order, so the two paths agree
+to FP32 rounding; the Cahn-Hilliard field does not depend on the work
+schedule at all (each output element is written by one item), so different
+slab lags give identical bits.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2507_21748_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def evx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_21748_gb300 import evx as E
+    return E
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_child(tmp_path, shape, nsteps, model, env_extra, seed=8, offset=0.2):
+    script = (
+        "import sys, numpy as np, torch\n"
+        "sys.path.insert(0, %r)\n"
+        "from paper_2507_21748_gb300 import evx, inputs\n"
+        "c0 = inputs.uniform_field(%r, seed=%d, offset=%r)\n"
+        "g = evx.Grid(%r, dt=0.1, M=1.0, kappa=1.0, h=1.0, model=%r)\n"
+        "g.set_field(torch.from_numpy(c0).cuda()); g.step(%d)\n"
+        "np.save(%r, g.get_field().cpu().numpy())\n"
+        "print(g.mean())\n"
+    ) % (ROOT, shape, seed, offset, shape, model, nsteps, str(tmp_path / "child.npy"))
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, "-c", script], check=True, env=env, capture_output=True, text=True)
+    return np.load(tmp_path / "child.npy"), float(r.stdout.split()[-1])
+
+
+def run_here(evx, shape, nsteps, model, seed=8, offset=0.2):
+    import torch
+    c0 = inputs.uniform_field(shape, seed=seed, offset=offset)
+    g = evx.Grid(shape, dt=0.1, M=1.0, kappa=1.0, h=1.0, model=model)
+    g.set_field(torch.from_numpy(c0).cuda())
+    g.step(nsteps)
+    out = g.get_field().cpu().numpy()
+    mean = g.mean()
+    g.close()
+    return out, mean
+
+
+FUSED_SHAPES = [(16, 256, 256), (64, 512, 512), (8, 1024, 1024), (24, 400, 400), (400, 400, 400), (40, 256, 256)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES)
+def test_fused_matches_separate_passes(evx, tmp_path, shape):
+    got, _ = run_here(evx, shape, 10, "ch")
+    sep, _ = run_child(tmp_path, shape, 10, "ch", {"EVX_NO_FUSE": "1"})
+    assert rel_l2(got, sep) <= 1e-6
+
+
+@pytest.mark.parametrize("lag", ["1", "8"])
+def test_fused_schedule_independent(evx, tmp_path, lag):
+    shape = (32, 512, 512)
+    got, _ = run_here(evx, shape, 7, "ch")
+    other, _ = run_child(tmp_path, shape, 7, "ch", {"EVX_FUSE_LAG": lag})
+    assert np.array_equal(got, other)
+
+
+@pytest.mark.parametrize("shape", [(16, 256, 256), (24, 400, 400)])
+def test_fused_one_step_vs_oracle(evx, shape):
+    c0 = inputs.uniform_field(shape, seed=0)
+    ref = O.ch_step(c0, 0.1, 1.0, 1.0, 1.0, 1)
+    got, _ = run_here(evx, shape, 1, "ch", seed=0, offset=0.0)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_fused_100_steps_vs_oracle(evx):
+    shape = (16, 256, 256)
+    c0 = inputs.uniform_field(shape, seed=0)
+    ref = O.ch_step(c0, 0.1, 1.0, 1.0, 1.0, 100, check_imag=False)
+    got, _ = run_here(evx, shape, 100, "ch", seed=0, offset=0.0)
+    assert rel_l2(got, ref) <= 1e-3
+
+
+def test_fused_allen_cahn(evx, tmp_path):
+    """Allen-Cahn: the fused pass also sums g(c) - g(cbar) per CTA for the mean update."""
+    shape = (16, 256, 256)
+    c0 = inputs.uniform_field(shape, seed=3, offset=0.1)
+    ref = O.ac_step(c0, 0.1, 1.0, 1.0, 1.0, 1)
+    got, mean = run_here(evx, shape, 1, "ac", seed=3, offset=0.1)
+    assert rel_l2(got, ref) <= 1e-5
+    assert abs(mean - ref.mean()) <= 1e-9
+    got10, mean10 = run_here(evx, shape, 10, "ac", seed=3, offset=0.1)
+    sep10, msep10 = run_child(tmp_path, shape, 10, "ac", {"EVX_NO_FUSE": "1"}, seed=3, offset=0.1)
+    assert rel_l2(got10, sep10) <= 1e-6
+    assert abs(mean10 - msep10) <= 1e-12
+
+
+def test_fused_pass_accounting(evx):
+    """With the fused pass, pass 1 reads S and writes W (2F of algorithmic bytes)
+    and passes 2 and 3 are empty; profiled steps report its time as pass 1."""
+    import torch
+    shape = (16, 256, 256)
+    g = evx.Grid(shape)
+    g.set_profiling(True)
+    g.set_field(torch.from_numpy(inputs.uniform_field(shape, seed=1)).cuda())
+    g.step(5)
+    ms, cnt = g.pass_times()
+    F = shape[0] * shape[1] * (shape[2] // 2 + 1) * 8
+    assert [g.pass_bytes(k) for k in range(4)] == [3.0 * F, 2.0 * F, 0.0, 0.0]
+    assert cnt == [5, 5, 5, 5] and ms[0] > 0 and ms[1] > 0
+    g.close()

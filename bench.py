@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-small", action="store_true", help="skip the 64^3 / 256^3 / 400^3 timings")
+    ap.add_argument("--no-design-b", action="store_true", help="skip the fused-pass (5-sweep) timing")
     ap.add_argument("--train-iters", type=int, default=500)
     ap.add_argument("--ac-steps", type=int, default=50, help="Allen-Cahn steps timed after the CH run (0: skip)")
     ap.add_argument("--vm-steps", type=int, default=20,
@@ -266,6 +267,53 @@ def bf16_peak():
         return float(d["bf16_tflops"]), "measured"
     except Exception:
         return 1900.0, "fallback"
+
+
+def adjoint_bench(n=128, nsteps=200, ckpt=20):
+    """The differentiable inverse run's cost: one gradient (adjoint of nsteps steps with
+    checkpoints every ckpt steps, forward recomputation included) against the forward
+    run alone, at n^3 with kappa = 1.5, M = 0.8 (the target configuration's parameters).
+    The gradient is checked against the FP64 oracle's adjoint on a 32^3 sample of the
+    same recipe (outside the timing)."""
+    import torch
+    from oracle import oracle as O
+    from paper_2507_21748_gb300 import evx, inputs
+    shape = (n, n, n)
+    c0 = torch.from_numpy(inputs.uniform_field(shape, seed=0)).cuda()
+    dL = torch.from_numpy(inputs.uniform_field(shape, seed=5, lo=-1.0, hi=1.0)).cuda()
+    g = evx.Grid(shape, dt=DT, M=0.8, kappa=1.5, h=H)
+    g.set_field(c0)
+    g.step(nsteps)  # builds the step graphs
+    g.adjoint(c0, nsteps, ckpt, dL)  # allocates the segment store
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g.set_field(c0)
+    g.step(nsteps)
+    out = g.get_field()
+    e1.record()
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    g0, gk, gm = g.adjoint(c0, nsteps, ckpt, dL)  # synchronises
+    t_adj = 1e3 * (time.perf_counter() - t0)
+    del out, g0
+    g.close()
+    # accuracy against the FP64 oracle adjoint (small sample of the same recipe)
+    m = 32
+    cs = inputs.uniform_field((m,) * 3, seed=0)
+    ds = inputs.uniform_field((m,) * 3, seed=5, lo=-1.0, hi=1.0)
+    gs = evx.Grid((m,) * 3, dt=DT, M=0.8, kappa=1.5, h=H)
+    a0, ak, am = gs.adjoint(torch.from_numpy(cs).cuda(), 40, ckpt, torch.from_numpy(ds).cuda())
+    gs.close()
+    r0, rk, rm = O.ch_adjoint(cs, ds, DT, 0.8, 1.5, H, 40)
+    a0 = a0.cpu().numpy()
+    return {"workload": "%d^3, %d steps, checkpoint every %d, kappa = 1.5, M = 0.8, dL/dc_N = U(-1, 1)"
+                        % (n, nsteps, ckpt),
+            "forward_ms": t_fwd, "gradient_ms": t_adj, "gradient_over_forward": t_adj / t_fwd,
+            "error_vs_oracle": {"what": "32^3, 40 steps, same recipe: FP32 GPU adjoint vs FP64 oracle adjoint",
+                                "dLdc0_rel_l2": float(np.linalg.norm(a0 - r0) / np.linalg.norm(r0)),
+                                "dLdkappa_rel": abs(ak - rk) / abs(rk), "dLdM_rel": abs(am - rm) / abs(rm)}}
 
 
 def surrogate_bench(args):
@@ -581,6 +629,43 @@ def main():
                       "growing mode; k = 0: FP64 sum of the FP32 field vs the input's" % len(modes))
     del c1
 
+    # ---- Design B: the same timed steps with the fused y-z-y pass (5 sweeps per step;
+    # opt-in, since on GB300 it is slower than the three separate passes)
+    design_b = None
+    if not args.no_design_b and not fused:
+        os.environ["EVX_FUSE"] = "1"
+        try:
+            gb = evx.Grid(shape, dt=DT, M=MOB, kappa=KAPPA, h=H, stream=stream)
+        finally:
+            os.environ.pop("EVX_FUSE", None)
+        if gb.pass_bytes(2) == 0.0:
+            gb.set_field(c0_dev)
+            gb.step(3)
+            gb.set_profiling(True)
+            gb.pass_times(reset=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            gb.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_b = e0.elapsed_time(e1)
+            pm, pc = gb.pass_times(reset=True)
+            gb.set_profiling(False)
+            gb.set_field(c0_dev)
+            gb.step(1)
+            c1 = gb.get_field().cpu().numpy()
+            design_b = {
+                "what": "x pass + fused y inverse/z step/y forward pass whose x slabs stay in L2 (5 sweeps of "
+                        "HBM traffic per step instead of 9)",
+                "value": job_throughput(1, args.steps, V, ms_b * 1e-3), "unit": UNIT,
+                "ms_per_step": ms_b / args.steps, "sweeps_per_step": sum(gb.pass_bytes(k) for k in range(4))
+                / field_bytes, "x_pass_ms": pm[0] / max(pc[0], 1), "fused_pass_ms": pm[1] / max(pc[1], 1),
+                "fused_kernel": "fused::fyzy_kernel<%d, %d, %d, %d>" % (r1, tp, rz, tz),
+                "error_vs_oracle": mode_error(O.dft_modes(c1, modes, "c"),
+                                              O.step_modes(c0, modes, DT, MOB, KAPPA, H), field_l2(c1))}
+            del c1
+        gb.close()
+
     # ---- end to end through the host API
     e2e = None
     if not args.no_e2e:
@@ -668,6 +753,12 @@ def main():
         except Exception as ex:  # report, do not fail the bench
             sur = {"error": repr(ex)}
 
+    adj = None
+    if not args.no_small and args.n == 1024:
+        try:
+            adj = adjoint_bench()
+        except Exception as ex:  # report, do not fail the bench
+            adj = {"error": repr(ex)}
     small = None
     if not args.no_small and args.n == 1024:
         try:
@@ -703,6 +794,7 @@ def main():
                                    "x pass 3 + y inverse 2 + z step 2 + y forward 2"),
                    "footprint_bytes": fp},
         "error_vs_oracle": err_ch,
+        "design_b": design_b,
         "roofline": {"bound": "hbm", "kernel": kern[dom] + " (" + names[dom] + ")",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_src + " hbm_gbs (copy)",
@@ -719,6 +811,7 @@ def main():
         "allen_cahn": ac,
         "variable_mobility": vm,
         "small_grids": small,
+        "adjoint": adj,
         "surrogate": sur,
     }
     print(json.dumps(out), flush=True)

@@ -47,13 +47,14 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
     if (tile >= ntiles) return;
     fill_twiddles<R1, TP>(tA, tB, a.tw, NTZ);
     for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
+    // rows to warps, 16-byte pieces of a row to lanes (no division by the runtime pitch)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     auto issue = [&](int tl) {
         const long long row0 = (long long)tl * RPC;
-        for (int e = threadIdx.x; e < RPC * Zh; e += NTZ) {
-            const int rr = e / Zh, q = e - rr * Zh;
+        for (int rr = warp; rr < RPC; rr += NTZ / 32) {
             const bool ok = row0 + rr < a.nrows;
-            const float2* src = a.in + (row0 + rr) * Zp + 2 * q;
-            cp_async16(buf + rr * BS + 2 * q, ok ? src : a.in, ok ? 16 : 0);
+            const float2* src = a.in + (ok ? (row0 + rr) * Zp : 0);
+            for (int q = lane; q < Zh; q += 32) cp_async16(buf + rr * BS + 2 * q, ok ? src + 2 * q : a.in, ok ? 16 : 0);
         }
         cp_commit();
     };
@@ -244,13 +245,14 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int n
         fill_twiddles<R1, TP>(tA, tB, a.tw, NTZ);
         for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
     }
+    // rows to warps, 16-byte pieces of a row to lanes (no division by the runtime pitch)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     auto issue = [&](int tl) {
         const long long row0 = (long long)tl * RPC;
-        for (int e = threadIdx.x; e < RPC * Zh; e += NTZ) {
-            const int rr = e / Zh, q = e - rr * Zh;
+        for (int rr = warp; rr < RPC; rr += NTZ / 32) {
             const bool ok = row0 + rr < a.nrows;
-            const float2* src = a.in + (row0 + rr) * Zp + 2 * q;
-            cp_async16(buf + rr * BS + 2 * q, ok ? src : a.in, ok ? 16 : 0);
+            const float2* src = a.in + (ok ? (row0 + rr) * Zp : 0);
+            for (int q = lane; q < Zh; q += 32) cp_async16(buf + rr * BS + 2 * q, ok ? src + 2 * q : a.in, ok ? 16 : 0);
         }
         cp_commit();
     };

@@ -78,18 +78,20 @@ struct FusedGeom {
 };
 
 // One y item: 8 columns (chunk) of all L rows of slab x, in -> 1D DFT along y -> out.
-// Element (x, y, kz) sits at base_x + (y / YB) os2 + (y % YB) Zp + kz.
-template <int R1, int TP, int DIR>
+// Element (x, y, kz) sits at base_x + (y / YB) os2 + (y % YB) Zp + kz (YB = a.YB,
+// a compile-time constant here: 32 for power-of-two edges, 16 for 400).
+template <int R1, int TP, int YB, int DIR>
 __device__ __forceinline__ void y_item(const float2* in, float2* out, long long base_x,
                                        const YZYArgs& a, int chunk, float2* buf, const float2* tA, const float2* tB) {
     constexpr int L = R1 * TP, NB = R1 / TP, NT = 8 * TP;
     const int p = threadIdx.x & 7, n2 = threadIdx.x >> 3;
     const int kz0 = chunk * 8;
-    // 16-byte pieces: 4 per row (columns kz0 + 2q, +1); columns past ncols are zero-filled
-    for (int e = threadIdx.x; e < L * 4; e += NT) {
-        const int y = e >> 2, q = e & 3, kz = kz0 + 2 * q;
-        const int nval = min(max(a.ncols - kz, 0), 2);
-        const long long off = base_x + (long long)(y / a.YB) * a.os2 + (long long)(y % a.YB) * a.Zp + kz;
+    // 16-byte pieces: 4 per row; thread t moves piece q = t % 4 (columns kz0 + 2q, +1;
+    // columns past ncols are zero-filled) of rows t / 4, t / 4 + NT / 4, ...
+    const int q = threadIdx.x & 3, kz = kz0 + 2 * q;
+    const int nval = min(max(a.ncols - kz, 0), 2);
+    for (int y = threadIdx.x >> 2; y < L; y += NT / 4) {
+        const long long off = base_x + (long long)(y / YB) * a.os2 + (y % YB) * a.Zp + kz;
         fast::cp_async16(buf + y * 8 + 2 * q, nval ? in + off : in, nval * 8);
     }
     fast::cp_commit();
@@ -109,10 +111,8 @@ __device__ __forceinline__ void y_item(const float2* in, float2* out, long long 
 #pragma unroll
         for (int c = 0; c < TP; ++c) buf[(n2 * NB + i + R1 * c) * 8 + p] = v[i * TP + c];
     __syncthreads();
-    for (int e = threadIdx.x; e < L * 4; e += NT) {
-        const int y = e >> 2, q = e & 3, kz = kz0 + 2 * q;
-        const int nval = min(max(a.ncols - kz, 0), 2);
-        const long long off = base_x + (long long)(y / a.YB) * a.os2 + (long long)(y % a.YB) * a.Zp + kz;
+    for (int y = threadIdx.x >> 2; y < L; y += NT / 4) {
+        const long long off = base_x + (long long)(y / YB) * a.os2 + (y % YB) * a.Zp + kz;
         const float2* src = buf + y * 8 + 2 * q;
         if (nval == 2)
             *reinterpret_cast<float4*>(out + off) = *reinterpret_cast<const float4*>(src);
@@ -132,9 +132,11 @@ __device__ __forceinline__ void z_item(float2* W, long long r0, const YZYArgs& a
     const int BS = TP + (((Zp > RS ? Zp : RS) - TP + 15) & ~15);
     float2* xz = buf + RPC * BS;  // [RPC][zxs(M, TP)] R2C partner rows (R1 != 32)
     const int n2 = threadIdx.x % TP, r = threadIdx.x / TP;
-    for (int e = threadIdx.x; e < RPC * Zh; e += NT) {
-        const int rr = e / Zh, q = e - rr * Zh;
-        fast::cp_async16(buf + rr * BS + 2 * q, W + (r0 + rr) * Zp + 2 * q, 16);
+    // rows to warps, 16-byte pieces of a row to lanes
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rr = warp; rr < RPC; rr += NT / 32) {
+        const float2* src = W + (r0 + rr) * Zp;
+        for (int q = lane; q < Zh; q += 32) fast::cp_async16(buf + rr * BS + 2 * q, src + 2 * q, 16);
     }
     fast::cp_commit();
     fast::cp_wait<0>();
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(8 * TPy, (512 / (8 * TPy)) > 0 ? 512 / (8 * TP
     fyzy_kernel(YZYArgs a) {
     using G = FusedGeom<R1y, TPy, R1z, TPz>;
     constexpr int L = G::L, NT = G::NT, M = G::M, RPC = G::RPC;
+    constexpr int YBc = R1y == 20 ? 16 : 32;  // the y block of the layout (fused_yzy_shape checks a.YB)
     static_assert(NT % TPz == 0 && RPC >= 1, "z rows per item");
     extern __shared__ __align__(16) float4 smem4[];
     float2* buf = reinterpret_cast<float2*>(smem4);
@@ -246,14 +249,14 @@ __global__ void __launch_bounds__(8 * TPy, (512 / (8 * TPy)) > 0 ? 512 / (8 * TP
             __syncthreads();
         }
         if (kind == 0) {
-            y_item<R1y, TPy, 1>(a.S, a.W, x * xs, a, idx, buf, tAy, tBy);
+            y_item<R1y, TPy, YBc, 1>(a.S, a.W, x * xs, a, idx, buf, tAy, tBy);
         } else if (kind == 1) {
             // rows y = RPC idx .. RPC idx + RPC - 1 of slab x (inside one y block)
             const int y0 = RPC * idx;
             const long long r0 = ((long long)(y0 / a.YB) * a.nx + x) * a.YB + y0 % a.YB;
             z_item<R1z, TPz, NT, GS>(a.W, r0, a, buf, tAz, tBz, rtws, gp, c3, gacc);
         } else {
-            y_item<R1y, TPy, -1>(a.W, a.W, x * xs, a, idx, buf, tAy, tBy);
+            y_item<R1y, TPy, YBc, -1>(a.W, a.W, x * xs, a, idx, buf, tAy, tBy);
         }
         if (kind < 2) {  // publish the item to the slab's next stage
             __syncthreads();
@@ -350,19 +353,18 @@ cudaError_t run_fyzy(const YZYArgs& a, cudaStream_t st, int* grid_used) {
 int fused_yzy_shape(int ny, int M, int YB) {
     // (ny, M) pairs with kernels: the fast y and z transforms of equal edges;
     // a z item's 16 rows must sit inside one y block
-    if (YB != choose_yblock(ny, true) || ny % 16 || YB % 16) return 0;
+    if (YB != choose_yblock(ny, true) || YB != (ny == 400 ? 16 : 32) || ny % 16) return 0;
     if ((ny == 1024 && M == 512) || (ny == 512 && M == 256) || (ny == 256 && M == 128) || (ny == 400 && M == 200))
         return 1;
     return 0;
 }
 
 bool fused_yzy_enabled() {
-    static int on = -1;
-    if (on < 0) {
-        const char* e = std::getenv("EVX_NO_FUSE");
-        on = (e && e[0] == '1') ? 0 : 1;
-    }
-    return on == 1 && fast_paths_enabled();
+    // opt-in, read when a grid is created: the fused pass moves 5 instead of 9
+    // sweeps per step but is slower than the three separate passes on GB300
+    // (it is issue- and barrier-bound, not bandwidth-bound)
+    const char* e = std::getenv("EVX_FUSE");
+    return e && e[0] == '1' && fast_paths_enabled();
 }
 
 size_t fused_ctl_ints(int nx) { return 2 + 2 * (size_t)nx; }

@@ -131,7 +131,7 @@ struct YZYArgs {
     int lag;                // slabs between a slab's stages in the ticket order
 };
 int fused_yzy_shape(int ny, int M, int YB);  // 1 if a fused kernel exists for this y / z geometry
-bool fused_yzy_enabled();                    // false under EVX_NO_FUSE=1 or EVX_GENERIC=1
+bool fused_yzy_enabled();                    // true under EVX_FUSE=1 (read at grid creation), unless EVX_GENERIC=1
 size_t fused_ctl_ints(int nx);
 cudaError_t launch_fused_yzy(const YZYArgs& a, cudaStream_t st, int* grid_used);
 int fused_yzy_grid(const YZYArgs& a);        // CTAs a launch may use (partials it may write)
@@ -162,6 +162,8 @@ cudaError_t launch_sum_field(const float* c, long long nrows, int rowlen, long l
                              double* partials, int nblocks, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, int n, double* out, double scale,
                                    cudaStream_t st);
+// subtract the mean of n complex values stride apart from each (one block, FP64 sum)
+cudaError_t launch_remove_k0(float2* line, int n, long long stride, cudaStream_t st);
 // out = a + b (complex arrays of n elements)
 cudaError_t launch_cadd(const float2* a, const float2* b, float2* out, long long n,
                         cudaStream_t st);

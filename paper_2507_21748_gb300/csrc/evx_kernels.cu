@@ -355,6 +355,35 @@ __global__ void __launch_bounds__(NT) sum_rows_kernel(const float* c, long long 
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// The k = 0 mode of a state that is spectral in y and z and real in x is the
+// x-sum of its (ky = 0, kz = 0) line: removing it subtracts the line's mean
+// from each of its n elements (stride apart). One block, FP64 sum.
+__global__ void __launch_bounds__(1024) remove_k0_kernel(float2* line, int n, long long stride) {
+    __shared__ double ws[32];
+    __shared__ double mre, mim;
+    double sr = 0.0, si = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) {
+        const float2 v = line[(long long)i * stride];
+        sr += (double)v.x;
+        si += (double)v.y;
+    }
+    sr = block_sum_double(sr, ws);
+    __syncthreads();
+    si = block_sum_double(si, ws);
+    if (threadIdx.x == 0) {
+        mre = sr / n;
+        mim = si / n;
+    }
+    __syncthreads();
+    const float fr = (float)mre, fi = (float)mim;
+    for (int i = threadIdx.x; i < n; i += 1024) {
+        float2 v = line[(long long)i * stride];
+        v.x -= fr;
+        v.y -= fi;
+        line[(long long)i * stride] = v;
+    }
+}
+
 __global__ void __launch_bounds__(1024) reduce_partials_kernel(const double* partials, int n,
                                                                 double* out, double scale) {
     __shared__ double ws[32];
@@ -596,6 +625,11 @@ int vm_energy_grid(int nx, int ny, int nparts) { return std::min(vm_grid(nx, ny)
 
 cudaError_t launch_ac_mean(const double* gsum, int n, double* cbar, double dtL, double invV, cudaStream_t st) {
     ac_mean_kernel<<<1, 1024, 0, st>>>(gsum, n, cbar, dtL, invV);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_remove_k0(float2* line, int n, long long stride, cudaStream_t st) {
+    remove_k0_kernel<<<1, 1024, 0, st>>>(line, n, stride);
     return cudaGetLastError();
 }
 

@@ -463,13 +463,13 @@ static evx_status load_real(evx_grid* g, const float* rows, long long pitch, int
     z.rin = rows;
     z.rpitch = pitch;
     z.map_rows = map;
-    z.out = g->W;
+    z.out = g->S;
     z.cbar = g->d_scal;  // transform c - cbar
     z.fast_ok = 1;
     CK(launch_zpass(z, Z_R2C, g->st));
-    CK(launch_spass(y_args(g, g->W, g->W), -1, g->st));
-    // x pass with a = 1, b = 0: removes the k = 0 mode (carried in FP64)
-    CK(launch_xupdate(x_args(g, nullptr, g->W, g->S, 0.0, 0.0, 0.0), g->st));
+    CK(launch_spass(y_args(g, g->S, g->S), -1, g->st));
+    // remove the k = 0 mode (carried in FP64): the mean of the (ky = 0, kz = 0) x line
+    CK(launch_remove_k0(g->S, g->nx, (long long)g->YB * g->Zp, g->st));
     g->has_field = true;
     g->steps = 0;
     return EVX_OK;
@@ -518,10 +518,10 @@ evx_status evx_set_field_host(evx_grid* g, const float* h_c) {
         g->steps = 0;
         return EVX_OK;
     }
-    // one contiguous copy into S's memory (the state is rebuilt from it: the R2C
-    // reads it before the x pass overwrites S), then the caller-order row map
-    CK(cudaMemcpyAsync(g->S, h_c, field_bytes(g), cudaMemcpyHostToDevice, g->st));
-    evx_status s = load_real(g, reinterpret_cast<const float*>(g->S), g->nz, 1);
+    // one contiguous copy into W's memory (the R2C reads the caller-order rows from
+    // there and writes the state S), then the caller-order row map
+    CK(cudaMemcpyAsync(g->W, h_c, field_bytes(g), cudaMemcpyHostToDevice, g->st));
+    evx_status s = load_real(g, reinterpret_cast<const float*>(g->W), g->nz, 1);
     if (s != EVX_OK) return s;
     CK(cudaStreamSynchronize(g->st));
     return EVX_OK;

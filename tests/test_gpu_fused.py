@@ -2,7 +2,8 @@
 one persistent kernel whose x slabs stay in L2) against the three separate
 passes and the FP64 oracle, through the C-ABI.
 
-The separate passes run in a child process with EVX_NO_FUSE=1. The fused
+The fused pass is opt-in (EVX_FUSE=1 when a grid is created); the separate
+passes run in a child process without it. The fused
 kernel applies the same transforms in the same order, so the two paths agree
 to FP32 rounding; the Cahn-Hilliard field does not depend on the work
 schedule at all (each output element is written by one item), so different
@@ -49,15 +50,25 @@ def run_child(tmp_path, shape, nsteps, model, env_extra, seed=8, offset=0.2):
         "np.save(%r, g.get_field().cpu().numpy())\n"
         "print(g.mean())\n"
     ) % (ROOT, shape, seed, offset, shape, model, nsteps, str(tmp_path / "child.npy"))
-    env = dict(os.environ, **env_extra)
+    env = {k: v for k, v in os.environ.items() if k != "EVX_FUSE"}
+    env.update(env_extra)
     r = subprocess.run([sys.executable, "-c", script], check=True, env=env, capture_output=True, text=True)
     return np.load(tmp_path / "child.npy"), float(r.stdout.split()[-1])
+
+
+def fused_grid(evx, shape, **kw):
+    os.environ["EVX_FUSE"] = "1"
+    try:
+        return evx.Grid(shape, **kw)
+    finally:
+        os.environ.pop("EVX_FUSE", None)
 
 
 def run_here(evx, shape, nsteps, model, seed=8, offset=0.2):
     import torch
     c0 = inputs.uniform_field(shape, seed=seed, offset=offset)
-    g = evx.Grid(shape, dt=0.1, M=1.0, kappa=1.0, h=1.0, model=model)
+    g = fused_grid(evx, shape, dt=0.1, M=1.0, kappa=1.0, h=1.0, model=model)
+    assert g.pass_bytes(2) == 0.0  # the fused pass is in use
     g.set_field(torch.from_numpy(c0).cuda())
     g.step(nsteps)
     out = g.get_field().cpu().numpy()
@@ -72,7 +83,7 @@ FUSED_SHAPES = [(16, 256, 256), (64, 512, 512), (8, 1024, 1024), (24, 400, 400),
 @pytest.mark.parametrize("shape", FUSED_SHAPES)
 def test_fused_matches_separate_passes(evx, tmp_path, shape):
     got, _ = run_here(evx, shape, 10, "ch")
-    sep, _ = run_child(tmp_path, shape, 10, "ch", {"EVX_NO_FUSE": "1"})
+    sep, _ = run_child(tmp_path, shape, 10, "ch", {})
     assert rel_l2(got, sep) <= 1e-6
 
 
@@ -80,7 +91,7 @@ def test_fused_matches_separate_passes(evx, tmp_path, shape):
 def test_fused_schedule_independent(evx, tmp_path, lag):
     shape = (32, 512, 512)
     got, _ = run_here(evx, shape, 7, "ch")
-    other, _ = run_child(tmp_path, shape, 7, "ch", {"EVX_FUSE_LAG": lag})
+    other, _ = run_child(tmp_path, shape, 7, "ch", {"EVX_FUSE_LAG": lag, "EVX_FUSE": "1"})
     assert np.array_equal(got, other)
 
 
@@ -109,9 +120,12 @@ def test_fused_allen_cahn(evx, tmp_path):
     assert rel_l2(got, ref) <= 1e-5
     assert abs(mean - ref.mean()) <= 1e-9
     got10, mean10 = run_here(evx, shape, 10, "ac", seed=3, offset=0.1)
-    sep10, msep10 = run_child(tmp_path, shape, 10, "ac", {"EVX_NO_FUSE": "1"}, seed=3, offset=0.1)
+    sep10, msep10 = run_child(tmp_path, shape, 10, "ac", {}, seed=3, offset=0.1)
     assert rel_l2(got10, sep10) <= 1e-6
-    assert abs(mean10 - msep10) <= 1e-12
+    # the FP32 per-tile sums of g(c) - g(cbar) are grouped differently (16-row items
+    # against 8-row tiles), so the FP64 means differ at the 1e-7 relative rounding
+    # of those sums times the mean's share of the update
+    assert abs(mean10 - msep10) <= 1e-10
 
 
 def test_fused_pass_accounting(evx):
@@ -119,7 +133,7 @@ def test_fused_pass_accounting(evx):
     and passes 2 and 3 are empty; profiled steps report its time as pass 1."""
     import torch
     shape = (16, 256, 256)
-    g = evx.Grid(shape)
+    g = fused_grid(evx, shape)
     g.set_profiling(True)
     g.set_field(torch.from_numpy(inputs.uniform_field(shape, seed=1)).cuda())
     g.step(5)

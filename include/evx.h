@@ -161,6 +161,20 @@ int evx_get_model(const evx_grid *g); /* -1 for NULL */
  * asynchronous, as evx_ch_step. */
 evx_status evx_step(evx_grid *g, int n_steps);
 
+/* One block of n_steps (1..4096) Cahn-Hilliard steps at the cost of one step:
+ * the scheme's stiff linear part is applied exactly over the block and its
+ * nonlinear remainder is frozen at the block's start. With d = c - cbar and
+ * g(c) = g(cbar) + g'(cbar) d + N(d), N = d^2 (3 cbar + d), the scheme above
+ * reads c_hat' = L c_hat + B N_hat (k != 0), L = (1 - dt M |k|^2 g'(cbar)) / D,
+ * B = -dt M |k|^2 / D; holding N_hat fixed,
+ *   c_hat_n = L^n c_hat_0 + B (sum_{j<n} L^j) N_hat_0,
+ * and the FP64 mean is unchanged. n_steps = 1 is one step of the scheme. This
+ * propagator is not the paper's: it is the base that the learned surrogate
+ * corrects (include/evx_nn.h). Four passes on the grid's stream, not captured
+ * in a graph; the step count advances by n_steps. EVX_ERR_STATE for another
+ * model or no field. */
+evx_status evx_ch_block(evx_grid *g, int n_steps);
+
 /* Ginzburg-Landau energy and mass of the current field, in FP64 (paper:
  * F_int of subsection "Phase transformations", in the c in [-1, 1] form):
  *   E    = h^3 sum_x (c^2 - 1)^2 / 4 + h^3 (kappa/2) (1/V) sum_k |k|^2 |c_hat(k)|^2
@@ -251,6 +265,16 @@ evx_status evx_step_count(const evx_grid *g, long long *steps);
  * save). */
 evx_status evx_save(evx_grid *g, const char *path);
 evx_status evx_load(evx_grid *g, const char *path);
+
+/* Bounds-checked debug build (libevx_bounds.so, compiled with
+ * -DEVX_BOUNDS_CHECK; a test facility, not part of the method): *enabled (may
+ * be NULL) is 1 in that build, 0 in the normal one. *line (may be NULL)
+ * receives the source line of the first global access that the mixed-radix,
+ * adjoint, reduction or variable-mobility kernels found outside its buffer
+ * since the last call (0 if none; the access was skipped, nothing trapped),
+ * and the record is cleared. With line non-NULL the call synchronises the
+ * device. The normal build has no checks and always reports 0. */
+evx_status evx_debug_bounds(int *enabled, int *line);
 
 /* Last error message of g (or of the calling thread when g is NULL). */
 const char *evx_last_error(const evx_grid *g);

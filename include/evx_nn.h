@@ -88,6 +88,26 @@ evx_status evx_nn_field_to_act(const float *f, long long nvox, int c, float scal
 evx_status evx_nn_zero_mean_add(const float *base, const float *d, int nsamples, long long V, double *partials,
                                 int nparts, float *out, void *stream);
 
+/* As evx_nn_zero_mean_add with the correction scaled per sample:
+ * out = base + scale[s] (d - mean_s(d)), scale a device array of nsamples doubles. */
+evx_status evx_nn_zero_mean_add_scaled(const float *base, const float *d, const double *scale, int nsamples,
+                                       long long V, double *partials, int nparts, float *out, void *stream);
+
+/* Relative strength of the nonlinear remainder of c^3 - c about each sample's
+ * mean (the part the block propagator of evx_ch_block freezes over a block):
+ *   scale[s] = min(1, ||N||_2 / ||d||_2),  d = c - mean(c),  N = d^2 (3 mean(c) + d),
+ * FP64, fixed summation order; 0 for a uniform sample. It is the learned
+ * surrogate's output scale (the network's correction cannot exceed what the
+ * nonlinearity can produce). nsamples <= 32 fields of V values, contiguous;
+ * partials: 3 nsamples nparts doubles; scale: nsamples device doubles. */
+evx_status evx_nn_nl_scale(const float *c, int nsamples, long long V, double *partials, int nparts, double *scale,
+                           void *stream);
+
+/* d_sum = sum |x| over n values in FP64 (device double), fixed summation order
+ * (nparts partials, then one sum); the guard's L1 norm of a sample, against which
+ * the mass drift of a surrogate block is measured. */
+evx_status evx_nn_abs_sum(const float *x, long long n, double *partials, int nparts, double *d_sum, void *stream);
+
 /* d_sum = sum (p - t)^2 in FP64 (device double); grad (may be NULL) = grad_scale (p - t). */
 evx_status evx_nn_mse(const float *p, const float *t, long long n, float grad_scale, float *grad,
                       double *partials, int nparts, double *d_sum, void *stream);

@@ -184,6 +184,35 @@ def ch_step_increment(c, dt, M, kappa, h=1.0, nsteps=1):
     return c
 
 
+def ch_block_step(c, dt, M, kappa, h=1.0, nsteps=10):
+    """One block of nsteps steps of the scheme with its stiff linear part exact
+    and its nonlinear remainder frozen at the block's start (the learned
+    surrogate's base propagator; a construct of this build, not the paper's).
+
+    Write the scheme's update (subsection "Semi-implicit timestepping",
+    S = -M kappa |k|^4) as c_hat' = (c_hat - dt M |k|^2 g_hat) / D and split
+    g(c) = g(cbar) + g'(cbar) d + N(d), d = c - cbar, N = d^2 (3 cbar + d). The
+    part linear in d is one multiplication per mode,
+        c_hat' = L c_hat + B N_hat,  L = (1 - dt M |k|^2 g'(cbar)) / D,  B = -dt M |k|^2 / D,
+    (k != 0; the mean cbar is conserved). Holding N_hat fixed over nsteps steps:
+        d_hat_n = L^n d_hat_0 + B (sum_{j<n} L^j) N_hat_0.
+    nsteps = 1 is exactly one step of the scheme.
+    """
+    c = np.asarray(c, dtype=np.float64)
+    cb = float(c.mean())
+    a, b, k2, D = symbols(c.shape, dt, M, kappa, h)
+    Lk = (1.0 - dt * M * k2 * (3.0 * cb * cb - 1.0)) / D
+    d = c - cb
+    P = np.ones_like(Lk)
+    Ssum = np.zeros_like(Lk)
+    for _ in range(nsteps):
+        Ssum += P
+        P = P * Lk
+    dh = P * fftn(d) + b * Ssum * fftn(d * d * (3.0 * cb + d))
+    dh[0, 0, 0] = 0.0
+    return cb + ifftn(dh).real
+
+
 def ac_step(c, dt, L, kappa, h=1.0, nsteps=1, energies=False, check_imag=True):
     """Advance c by nsteps semi-implicit spectral Allen-Cahn steps (FP64).
 

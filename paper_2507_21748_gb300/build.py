@@ -41,16 +41,23 @@ def _deps_mtime():
     return m
 
 
-def build_lib(force=False, verbose=False, jobs=None):
+LIB_BOUNDS = os.path.join(OUT_DIR, "libevx_bounds.so")
+
+
+def build_lib(force=False, verbose=False, jobs=None, debug_bounds=False):
+    """Build libevx.so, or with debug_bounds=True the bounds-checked
+    libevx_bounds.so (-DEVX_BOUNDS_CHECK; objects in _lib/bounds/)."""
     sources = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    lib_path = LIB_BOUNDS if debug_bounds else LIB
+    obj_dir = os.path.join(OUT_DIR, "bounds") if debug_bounds else OUT_DIR
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= _deps_mtime():
+        return lib_path
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
-    flags = _flags()
+    flags = _flags(debug_bounds)
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         cmd = [nvcc] + flags + ["-I", os.path.join(HERE, "..", "include"), "-c",
                                 os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -62,13 +69,13 @@ def build_lib(force=False, verbose=False, jobs=None):
 
     with cf.ThreadPoolExecutor(max_workers=jobs or len(sources)) as ex:
         objs = list(ex.map(compile_one, sources))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib_path + ".tmp%d" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -28,6 +28,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "evx_grid_impl.h"
 
 using namespace evx;
@@ -70,18 +72,20 @@ __device__ __forceinline__ double block_sum_d(double v, double* ws) {
 }
 
 __device__ __forceinline__ void load_cols(float2* tile, int c0, const float2* g, long long base,
-                                          long long rs, int L, int col0, int ncols) {
+                                          long long rs, int L, int col0, int ncols, long long nbuf) {
     for (int e = threadIdx.x; e < L * SP; e += NT) {
         const int i = e / SP, p = e % SP;
-        tile[i * (2 * SP) + c0 + p] = (col0 + p < ncols) ? g[base + i * rs + p] : make_float2(0.f, 0.f);
+        const long long idx = base + i * rs + p;
+        tile[i * (2 * SP) + c0 + p] = (col0 + p < ncols && EVX_IN(idx, nbuf)) ? g[idx] : make_float2(0.f, 0.f);
     }
 }
 
 __device__ __forceinline__ void store_cols(float2* g, const float2* tile, int c0, long long base,
-                                           long long rs, int L, int col0, int ncols) {
+                                           long long rs, int L, int col0, int ncols, long long nbuf) {
     for (int e = threadIdx.x; e < L * SP; e += NT) {
         const int i = e / SP, p = e % SP;
-        if (col0 + p < ncols) g[base + i * rs + p] = tile[i * (2 * SP) + c0 + p];
+        const long long idx = base + i * rs + p;
+        if (col0 + p < ncols && EVX_IN(idx, nbuf)) g[idx] = tile[i * (2 * SP) + c0 + p];
     }
 }
 
@@ -102,8 +106,9 @@ __global__ void __launch_bounds__(NT, 1) xadj_kernel(XAdjArgs a) {
     const int chunk = blockIdx.x, ky = blockIdx.y;
     const int col0 = chunk * SP;
     const long long base = split_off(ky, a.YB, a.os, a.os2) + col0;
-    load_cols(tile, 0, a.Lam, base, a.rs, L, col0, a.ncols);
-    load_cols(tile, SP, a.Sn1, base, a.rs, L, col0, a.ncols);
+    const long long nbuf = (long long)(a.ny / a.YB) * a.os2;  // complex elements of each field
+    load_cols(tile, 0, a.Lam, base, a.rs, L, col0, a.ncols, nbuf);
+    load_cols(tile, SP, a.Sn1, base, a.rs, L, col0, a.ncols, nbuf);
     __syncthreads();
     fft_cols2<-1>(tile, L, a.plan, tws);
     fft_cols2<-1>(tile + SP, L, a.plan, tws);
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(NT, 1) xadj_kernel(XAdjArgs a) {
         }
     }
     __syncthreads();
-    load_cols(tile, SP, a.Gn, base, a.rs, L, col0, a.ncols);
+    load_cols(tile, SP, a.Gn, base, a.rs, L, col0, a.ncols, nbuf);
     __syncthreads();
     fft_cols2<-1>(tile + SP, L, a.plan, tws);
     for (int e = threadIdx.x; e < L * SP; e += NT) {
@@ -146,8 +151,8 @@ __global__ void __launch_bounds__(NT, 1) xadj_kernel(XAdjArgs a) {
     __syncthreads();
     fft_cols2<1>(tile, L, a.plan, tws);
     fft_cols2<1>(tile + SP, L, a.plan, tws);
-    store_cols(a.P, tile, 0, base, a.rs, L, col0, a.ncols);
-    store_cols(a.T, tile, SP, base, a.rs, L, col0, a.ncols);
+    store_cols(a.P, tile, 0, base, a.rs, L, col0, a.ncols, nbuf);
+    store_cols(a.T, tile, SP, base, a.rs, L, col0, a.ncols, nbuf);
     const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
     const long long nblk = (long long)gridDim.x * gridDim.y;
     acc_k = block_sum_d(acc_k, ws);
@@ -172,6 +177,21 @@ __global__ void __launch_bounds__(1024) accum_partials_kernel(const double* part
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if (threadIdx.x == 0) *out += acc * scale;
     }
+}
+
+int bounds_line_adjoint(bool clear) {
+#ifdef EVX_BOUNDS_CHECK
+    int h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_bounds_line, sizeof(int)) != cudaSuccess) return -1;
+    if (clear && h) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_bounds_line, &z, sizeof(int));
+    }
+    return h;
+#else
+    (void)clear;
+    return 0;
+#endif
 }
 
 }  // namespace evx
@@ -277,6 +297,10 @@ extern "C" evx_status evx_ch_adjoint(evx_grid* g, const float* d_c0, int n_steps
                                      const float* d_dLdcN, float* d_dLdc0, double* dLdkappa,
                                      double* dLdM) {
     if (!g || !d_c0 || !d_dLdcN || !d_dLdc0) return set_error(g, EVX_ERR_ARG, "NULL argument");
+    nvtxRangePushA("evx_ch_adjoint");
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop_;
     if (g->model != EVX_MODEL_CH)
         return set_error(g, EVX_ERR_STATE, "the adjoint is implemented for the Cahn-Hilliard model only");
     if (n_steps < 0 || ckpt_every < 1) return set_error(g, EVX_ERR_ARG, "bad n_steps / ckpt_every");

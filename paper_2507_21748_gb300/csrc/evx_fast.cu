@@ -24,10 +24,12 @@
 namespace evx {
 namespace fast {
 // ------------------------------------------------ z pass: C2R, c^3 - c, R2C
-template <int R1, int TP, int NTZ, bool GS>
+template <int R1, int TP, int NTZ, bool GS, bool ADJ>
 __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int ntiles) {
     // GS (Allen-Cahn): also sum g(c) - g(cbar) over the grid, FP32 per thread and
-    // tile, FP64 across tiles, one FP64 partial per CTA in a.gsum[blockIdx.x]
+    // tile, FP64 across tiles, one FP64 partial per CTA in a.gsum[blockIdx.x].
+    // ADJ (the adjoint's z pass): the pointwise stage multiplies the real field by
+    // g'(c_n) = 3 c_n^2 - 1, c_n read from the real rows a.cn (memory row order)
     constexpr int M = R1 * TP, NB = R1 / TP, RPC = NTZ / TP, ZPAD = zpad(R1, TP), RS = M + TP * ZPAD;
     extern __shared__ float4 smem4[];
     const int Zp = a.Zp, Zh = a.Zp / 2;
@@ -62,7 +64,9 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
     const double cbd = a.cbar ? *a.cbar : 0.0;
     const float cb = (float)cbd;
     const float cbl = (float)(cbd - (double)cb);
-    const float gp = (float)(3.0 * cbd * cbd - 1.0);  // g'(cbar)
+    // g'(cbar); 0 with a.nl_only: the pass then forms the nonlinear remainder
+    // N = d^2 (3 cbar + d) alone (the block propagator's input)
+    const float gp = a.nl_only ? 0.f : (float)(3.0 * cbd * cbd - 1.0);
     const float c3 = (float)(3.0 * cbd);
     const float s = a.scale;
     auto slot = [&](int rr, int nn, int aa) { return rr * BS + aa * TP + nn + aa / NB * ZPAD; };
@@ -107,6 +111,12 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
             for (int c = 0; c < TP; ++c) {
                 const float2 z = v[i * TP + c];
                 const float d0 = z.x * s, d1 = z.y * s;  // c - cbar (the state has no k = 0 mode)
+                if (ADJ) {  // lambda-side field times g'(c_n)
+                    const float2 cn = rowok ? reinterpret_cast<const float2*>(a.cn + row * a.cnpitch)[n2 * NB + i + R1 * c]
+                                            : make_float2(0.f, 0.f);
+                    v[i * TP + c] = make_float2(d0 * fmaf(3.f * cn.x, cn.x, -1.f), d1 * fmaf(3.f * cn.y, cn.y, -1.f));
+                    continue;
+                }
                 if (a.rout && rowok)
                     reinterpret_cast<float2*>(a.rout + row * a.rpitch)[n2 * NB + i + R1 * c] =
                         make_float2(fmaf(z.x, s, cbl) + cb, fmaf(z.y, s, cbl) + cb);
@@ -488,7 +498,8 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
 
 // x pass + update with TMA: boxes {8, 1, BOX (x), 1} of 8 columns. MODE 0:
 // Cahn-Hilliard, 1: Allen-Cahn, 2: preconditioner only (S' = F_x^-1 (dt / (1 +
-// dt M0 kappa |k|^4) F_x W), S not read; the variable-mobility model's spectral step).
+// dt M0 kappa |k|^4) F_x W), S not read; the variable-mobility model's spectral step),
+// 3: Cahn-Hilliard block propagator (evx_ch_block).
 // Two tile buffers, (L + TP) x 8 each, receive W and S by TMA. SEP (L = 1024):
 // a third buffer of the same size takes the transposes and stages the result,
 // and each field's next tile is loaded as soon as the current one is in
@@ -538,7 +549,21 @@ __global__ void __launch_bounds__(8 * TP, SEP ? 1 : (8 * TP >= 128 ? 3 : 1))
         for (int b = 0; b < NBOX; ++b)
             tma_load4(buf + b * BOX * P, m, chunk * P, ky % YB, b * BOX, ky / YB, bar);
     };
-    constexpr bool AC = MODE == 1, PRE = MODE == 2;
+    constexpr bool AC = MODE == 1, PRE = MODE == 2, BLK = MODE == 3;
+    // MODE 3 (block of a.nblk steps, linear part exact, nonlinear remainder frozen):
+    // L = (1 - dt M |k|^2 g'(cbar)) / D, c_hat' = L^n c_hat + B (sum_{j<n} L^j) N_hat
+    const float gpb = BLK ? (float)(3.0 * (*a.cbar) * (*a.cbar) - 1.0) : 0.f;
+    auto blk = [&](float k2, float& Pn, float& BS) {
+        const float Dinv = rcp_approx(fmaf(a.dtMk, k2 * k2, 1.f));
+        const float Lk = fmaf(-a.dtM * k2, gpb, 1.f) * Dinv;
+        float P = 1.f, S = 0.f;
+        for (int j = 0; j < a.nblk; ++j) {
+            S += P;
+            P *= Lk;
+        }
+        Pn = P;
+        BS = -a.dtM * k2 * Dinv * S;
+    };
     if (threadIdx.x == 0) {
         issue(&mW, bufW, bars + 0, tile);
         if (!PRE) issue(&mS, bufS, bars + 1, tile);
@@ -579,9 +604,16 @@ __global__ void __launch_bounds__(8 * TP, SEP ? 1 : (8 * TP >= 128 ? 3 : 1))
 #pragma unroll
                     for (int c = 0; c < TP; ++c) {
                         const float k2g = (SEP ? k2x[n2 * NB + i + R1 * c] : __ldg(k2x + n2 * NB + i + R1 * c)) + k2yz;
-                        const float fa = PRE  ? a.dtM * a.invL * rcp_approx(fmaf(a.dtMk, k2g * k2g, 1.f))
-                                         : AC ? ndtM
-                                              : ndtM * k2g;
+                        float fa;
+                        if (BLK) {
+                            float Pn;
+                            blk(k2g, Pn, fa);
+                            fa *= a.invL;
+                        } else {
+                            fa = PRE  ? a.dtM * a.invL * rcp_approx(fmaf(a.dtMk, k2g * k2g, 1.f))
+                                 : AC ? ndtM
+                                      : ndtM * k2g;
+                        }
                         G[i * TP + c] = cscale(v[i * TP + c], fa);
                     }
             } else {
@@ -590,8 +622,14 @@ __global__ void __launch_bounds__(8 * TP, SEP ? 1 : (8 * TP >= 128 ? 3 : 1))
 #pragma unroll
                     for (int c = 0; c < TP; ++c) {
                         const float k2 = (SEP ? k2x[n2 * NB + i + R1 * c] : __ldg(k2x + n2 * NB + i + R1 * c)) + k2yz;
-                        const float fa = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
-                        v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), fa);
+                        if (BLK) {
+                            float Pn, BS;
+                            blk(k2, Pn, BS);
+                            v[i * TP + c] = cadd(cscale(v[i * TP + c], Pn * a.invL), G[i * TP + c]);
+                        } else {
+                            const float fa = a.invL * rcp_approx(fmaf(a.dtMk, AC ? k2 : k2 * k2, 1.f));
+                            v[i * TP + c] = cscale(cadd(v[i * TP + c], G[i * TP + c]), fa);
+                        }
                     }
             }
         }
@@ -755,7 +793,8 @@ static bool run_fxupd_tma(const XUpdArgs& a, cudaStream_t st, cudaError_t* err) 
         sizeof(float2) * ((SEP ? 3 : 2) * (size_t)(L + TP) * 8 + (R1 == TP ? 1 : 2) * (size_t)L) +
         (SEP ? sizeof(float) * L : 0) + 16;
     int per = 0;
-    auto kern = a.model == 2   ? fast::fxupd_tma_kernel<R1, TP, 2, SEP>
+    auto kern = a.model == 3   ? fast::fxupd_tma_kernel<R1, TP, 3, SEP>
+                : a.model == 2 ? fast::fxupd_tma_kernel<R1, TP, 2, SEP>
                 : a.model == 1 ? fast::fxupd_tma_kernel<R1, TP, 1, SEP>
                                : fast::fxupd_tma_kernel<R1, TP, 0, SEP>;
     cudaError_t e = prep(kern, smem, 8 * TP, &per);
@@ -809,11 +848,13 @@ static size_t zpass_smem(int Zp) {
 }
 
 template <int R1, int TP>
-static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st, int* grid_used) {
+static cudaError_t run_fzstep(const ZPassArgs& a, cudaStream_t st, int* grid_used, bool adj = false) {
     constexpr int NTZ = ntz_of<R1, TP>(), RPC = NTZ / TP;
     const size_t smem = zpass_smem<R1, TP>(a.Zp);
     int per = 0;
-    auto kern = a.gsum ? fast::fzstep_kernel<R1, TP, NTZ, true> : fast::fzstep_kernel<R1, TP, NTZ, false>;
+    auto kern = adj       ? fast::fzstep_kernel<R1, TP, NTZ, false, true>
+                : a.gsum ? fast::fzstep_kernel<R1, TP, NTZ, true, false>
+                         : fast::fzstep_kernel<R1, TP, NTZ, false, false>;
     cudaError_t e = prep(kern, smem, NTZ, &per);
     if (e != cudaSuccess) return e;
     const int ntiles = (int)((a.nrows + RPC - 1) / RPC);
@@ -858,13 +899,14 @@ bool fast_zconv(const ZPassArgs& a, int dir, cudaStream_t st, cudaError_t* err, 
     return false;
 }
 
-bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used) {
+bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used, bool adj) {
+    if (adj && (!a.cn || (a.cnpitch & 1) || ((uintptr_t)a.cn & 7))) return false;
     switch (a.M) {
-        case 64: *err = run_fzstep<32, 2>(a, st, grid_used); return true;
-        case 128: *err = run_fzstep<32, 4>(a, st, grid_used); return true;
-        case 256: *err = run_fzstep<32, 8>(a, st, grid_used); return true;
-        case 512: *err = run_fzstep<32, 16>(a, st, grid_used); return true;
-        case 200: *err = run_fzstep<20, 10>(a, st, grid_used); return true;
+        case 64: *err = run_fzstep<32, 2>(a, st, grid_used, adj); return true;
+        case 128: *err = run_fzstep<32, 4>(a, st, grid_used, adj); return true;
+        case 256: *err = run_fzstep<32, 8>(a, st, grid_used, adj); return true;
+        case 512: *err = run_fzstep<32, 16>(a, st, grid_used, adj); return true;
+        case 200: *err = run_fzstep<20, 10>(a, st, grid_used, adj); return true;
     }
     return false;
 }

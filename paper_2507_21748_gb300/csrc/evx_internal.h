@@ -6,6 +6,27 @@
 
 namespace evx {
 
+// Bounds-checked debug build (-DEVX_BOUNDS_CHECK, libevx_bounds.so): the global
+// loads and stores of the mixed-radix, adjoint, reduction and variable-mobility
+// kernels test their index against the buffer's extent. An access outside it is
+// skipped (a load yields zero) and the first offending source line is kept in a
+// device word of the translation unit, reported by evx_debug_bounds(). There is
+// no trap: the kernel completes and the context stays usable. In the normal
+// build the predicate is the constant true.
+#ifdef EVX_BOUNDS_CHECK
+static __device__ int g_bounds_line;
+__device__ __forceinline__ bool evx_in_bounds(long long i, long long n, int line) {
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&g_bounds_line, 0, line);
+    return false;
+}
+#define EVX_IN(i, n) ::evx::evx_in_bounds((long long)(i), (long long)(n), __LINE__)
+#else
+#define EVX_IN(i, n) true
+#endif
+int bounds_line_kernels(bool clear);   // evx_kernels.cu (0 in the normal build)
+int bounds_line_adjoint(bool clear);   // evx_adjoint.cu
+
 // Spectral buffers are y-blocked: element (x, y, kz) of a half spectrum sits at
 //   ((y / YB * nx + x) * YB + y % YB) * Zp + kz      (complex64 units)
 // with YB = 32 when the y pass has a fast path (ny a power of two >= 64) and
@@ -61,7 +82,12 @@ struct XUpdArgs {
                         // 1 Allen-Cahn:    b = -dt L,       D = 1 + dt L kappa |k|^2
                         // 2 preconditioner: S_out = F_x^-1 dt / (1 + dtMk |k|^4) F_x W / L,
                         //   S not read (dtM holds dt)
+                        // 3 Cahn-Hilliard block of nblk steps (evx_ch_block): with
+                        //   L = (1 - dt M |k|^2 g'(cbar)) / D, B = -dt M |k|^2 / D,
+                        //   S' = F_x^-1 [L^n F_x S + B sum_{j<n} L^j F_x W] / L_x (W: F_y F_z N)
     int generic;        // 1: mixed-radix kernel only (no fast path, no bounded waits)
+    int nblk;           // model 3: steps per block
+    const double* cbar; // model 3: FP64 mean (for g'(cbar))
 };
 
 // Energy: gradient term sum_k w(kz) |k|^2 |c_hat|^2 from the state S.
@@ -107,6 +133,7 @@ struct ZPassArgs {
     // row r of the y-blocked spectrum is caller row x * ny + y
     int map_rows, YB, nxr, nyr;
     int generic;            // 1: mixed-radix kernel only (no fast path)
+    int nl_only;            // Z_STEP: form N = d^2 (3 cbar + d) instead of g(c) - g(cbar)
 };
 __host__ __device__ inline long long user_row(long long r, int YB, int nx, int ny) {
     const long long x = (r / YB) % nx, yb = r / ((long long)YB * nx), yi = r % YB;
@@ -172,7 +199,7 @@ constexpr int SUM_BLOCKS = 1216;  // 8 x 152 SMs
 // fast paths for power-of-two lengths (evx_fast.cu); return false if not applicable
 bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err);
 bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err);
-bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used);
+bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used, bool adj = false);
 bool fast_zconv(const ZPassArgs& a, int dir, cudaStream_t st, cudaError_t* err, int* grid_used);
 bool fast_paths_enabled();  // false when the environment sets EVX_GENERIC=1
 // reads (and optionally clears) the flag a bounded TMA wait sets when it gives up

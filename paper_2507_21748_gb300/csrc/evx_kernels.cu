@@ -57,17 +57,20 @@ __global__ void __launch_bounds__(NT, 2) spass_kernel(SPassArgs a) {
     const long long base = (long long)outer * a.os + (long long)chunk * SP;
     const int col0 = chunk * SP;
     const bool full = col0 + SP <= a.ncols;
+    const long long nbuf = (long long)(a.L / a.YB) * a.os2;  // complex elements of in / out
     if (full) {
         for (int e = threadIdx.x; e < a.L * (SP / 2); e += NT) {
             const int i = e / (SP / 2), q = e % (SP / 2);
-            const float4 v = *reinterpret_cast<const float4*>(a.in + base + split_off(i, a.YB, a.rs, a.os2) + 2 * q);
+            const long long idx = base + split_off(i, a.YB, a.rs, a.os2) + 2 * q;
+            const float4 v = EVX_IN(idx + 1, nbuf) ? *reinterpret_cast<const float4*>(a.in + idx)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
             reinterpret_cast<float4*>(tile)[e] = v;
         }
     } else {
         for (int e = threadIdx.x; e < a.L * SP; e += NT) {
             const int i = e / SP, p = e % SP;
-            tile[e] = (col0 + p < a.ncols) ? a.in[base + split_off(i, a.YB, a.rs, a.os2) + p]
-                                           : make_float2(0.f, 0.f);
+            const long long idx = base + split_off(i, a.YB, a.rs, a.os2) + p;
+            tile[e] = (col0 + p < a.ncols && EVX_IN(idx, nbuf)) ? a.in[idx] : make_float2(0.f, 0.f);
         }
     }
     __syncthreads();
@@ -75,31 +78,34 @@ __global__ void __launch_bounds__(NT, 2) spass_kernel(SPassArgs a) {
     if (full) {
         for (int e = threadIdx.x; e < a.L * (SP / 2); e += NT) {
             const int i = e / (SP / 2), q = e % (SP / 2);
-            *reinterpret_cast<float4*>(a.out + base + split_off(i, a.YB, a.rs, a.os2) + 2 * q) =
-                reinterpret_cast<const float4*>(tile)[e];
+            const long long idx = base + split_off(i, a.YB, a.rs, a.os2) + 2 * q;
+            if (EVX_IN(idx + 1, nbuf)) *reinterpret_cast<float4*>(a.out + idx) = reinterpret_cast<const float4*>(tile)[e];
         }
     } else {
         for (int e = threadIdx.x; e < a.L * SP; e += NT) {
             const int i = e / SP, p = e % SP;
-            if (col0 + p < a.ncols) a.out[base + split_off(i, a.YB, a.rs, a.os2) + p] = tile[e];
+            const long long idx = base + split_off(i, a.YB, a.rs, a.os2) + p;
+            if (col0 + p < a.ncols && EVX_IN(idx, nbuf)) a.out[idx] = tile[e];
         }
     }
 }
 
 // load SP columns of an x line into tile columns [c0, c0+SP) of a [L][2SP] tile
 __device__ __forceinline__ void load_x_cols(float2* tile, int c0, const float2* g, long long base,
-                                            long long rs, int L, int col0, int ncols) {
+                                            long long rs, int L, int col0, int ncols, long long nbuf) {
     if (col0 + SP <= ncols) {
         for (int e = threadIdx.x; e < L * (SP / 2); e += NT) {
             const int i = e / (SP / 2), q = e % (SP / 2);
-            const float4 v = *reinterpret_cast<const float4*>(g + base + i * rs + 2 * q);
+            const long long idx = base + i * rs + 2 * q;
+            const float4 v = EVX_IN(idx + 1, nbuf) ? *reinterpret_cast<const float4*>(g + idx)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
             *reinterpret_cast<float4*>(tile + i * (2 * SP) + c0 + 2 * q) = v;
         }
     } else {
         for (int e = threadIdx.x; e < L * SP; e += NT) {
             const int i = e / SP, p = e % SP;
-            tile[i * (2 * SP) + c0 + p] =
-                (col0 + p < ncols) ? g[base + i * rs + p] : make_float2(0.f, 0.f);
+            const long long idx = base + i * rs + p;
+            tile[i * (2 * SP) + c0 + p] = (col0 + p < ncols && EVX_IN(idx, nbuf)) ? g[idx] : make_float2(0.f, 0.f);
         }
     }
 }
@@ -116,8 +122,11 @@ __global__ void __launch_bounds__(NT, 1) xupdate_kernel(XUpdArgs a) {
     const long long base = split_off(ky, a.YB, a.os, a.os2) + col0;
     const bool haveW = a.W != nullptr;
     const bool pre = a.model == 2;  // preconditioner only: S' = F_x^-1 (dt / (1 + dt M0 kappa |k|^4)) F_x W
-    if (haveW) load_x_cols(tile, 0, a.W, base, a.rs, L, col0, a.ncols);
-    if (!pre) load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols);
+    const bool blk = a.model == 3;  // block propagator: L^n c_hat + B (sum_{j<n} L^j) N_hat
+    const float gpb = blk ? (float)(3.0 * (*a.cbar) * (*a.cbar) - 1.0) : 0.f;
+    const long long nbuf = (long long)(a.ny / a.YB) * a.os2;  // complex elements of W, S, S_out
+    if (haveW) load_x_cols(tile, 0, a.W, base, a.rs, L, col0, a.ncols, nbuf);
+    if (!pre) load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols, nbuf);
     __syncthreads();
     if (haveW) fft_cols<-1>(tile, L, 2 * SP, a.plan, tws);
     if (!pre) fft_cols<-1>(tile + SP, L, 2 * SP, a.plan, tws);
@@ -133,7 +142,17 @@ __global__ void __launch_bounds__(NT, 1) xupdate_kernel(XUpdArgs a) {
             const float b = -a.dtM * (a.model == 1 ? 1.f : k2) * ainv;
             const float2 c = pre ? make_float2(0.f, 0.f) : tile[i * (2 * SP) + SP + p];
             float2 r = make_float2(ainv * c.x, ainv * c.y);
-            if (pre) {  // dtM holds dt here: r = dt / (1 + dt M0 kappa |k|^4) g_hat / L
+            if (blk) {  // L = (1 - dt M |k|^2 g'(cbar)) / D; ainv = invL / D
+                const float Lk = fmaf(-a.dtM * k2, gpb, 1.f) * ainv * (float)L;
+                float P = 1.f, S = 0.f;
+                for (int j = 0; j < a.nblk; ++j) {
+                    S += P;
+                    P *= Lk;
+                }
+                const float2 gh = tile[i * (2 * SP) + p];
+                const float bs = -a.dtM * k2 * ainv * S;
+                r = make_float2(fmaf(bs, gh.x, P * a.invL * c.x), fmaf(bs, gh.y, P * a.invL * c.y));
+            } else if (pre) {  // dtM holds dt here: r = dt / (1 + dt M0 kappa |k|^4) g_hat / L
                 const float2 gh = tile[i * (2 * SP) + p];
                 r = make_float2(a.dtM * ainv * gh.x, a.dtM * ainv * gh.y);
             } else if (haveW) {
@@ -150,13 +169,15 @@ __global__ void __launch_bounds__(NT, 1) xupdate_kernel(XUpdArgs a) {
     if (col0 + SP <= a.ncols) {
         for (int e = threadIdx.x; e < L * (SP / 2); e += NT) {
             const int i = e / (SP / 2), q = e % (SP / 2);
-            *reinterpret_cast<float4*>(a.S_out + base + i * a.rs + 2 * q) =
-                *reinterpret_cast<const float4*>(tile + i * (2 * SP) + SP + 2 * q);
+            const long long idx = base + i * a.rs + 2 * q;
+            if (EVX_IN(idx + 1, nbuf))
+                *reinterpret_cast<float4*>(a.S_out + idx) = *reinterpret_cast<const float4*>(tile + i * (2 * SP) + SP + 2 * q);
         }
     } else {
         for (int e = threadIdx.x; e < L * SP; e += NT) {
             const int i = e / SP, p = e % SP;
-            if (col0 + p < a.ncols) a.S_out[base + i * a.rs + p] = tile[i * (2 * SP) + SP + p];
+            const long long idx = base + i * a.rs + p;
+            if (col0 + p < a.ncols && EVX_IN(idx, nbuf)) a.S_out[idx] = tile[i * (2 * SP) + SP + p];
         }
     }
 }
@@ -172,7 +193,7 @@ __global__ void __launch_bounds__(NT, 1) xenergy_kernel(XEnergyArgs a) {
     const int chunk = blockIdx.x, ky = blockIdx.y;
     const int col0 = chunk * SP;
     const long long base = split_off(ky, a.YB, a.os, a.os2) + col0;
-    load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols);
+    load_x_cols(tile, SP, a.S, base, a.rs, L, col0, a.ncols, (long long)(a.ny / a.YB) * a.os2);
     __syncthreads();
     fft_cols<-1>(tile + SP, L, 2 * SP, a.plan, tws);
     const double k2y = a.k2y[ky];
@@ -219,7 +240,8 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
             float2 x = make_float2(0.f, 0.f);
             if (r < nr) {
                 const long long rr = a.map_rows ? user_row(row0 + r, a.YB, a.nxr, a.nyr) : row0 + r;
-                x = reinterpret_cast<const float2*>(a.rin + rr * a.rpitch)[n];
+                if (EVX_IN(rr * a.rpitch + 2 * n + 1, a.nrows * a.rpitch))
+                    x = reinterpret_cast<const float2*>(a.rin + rr * a.rpitch)[n];
                 x = make_float2((x.x - cb) - cbl, (x.y - cb) - cbl);
             }
             tile[r * PZ + n] = x;
@@ -228,7 +250,8 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
     } else {
         for (int e = threadIdx.x; e < rows * (M + 1); e += NT) {
             const int r = e / (M + 1), i = e - r * (M + 1);
-            tile[r * PZ + i] = r < nr ? a.in[(row0 + r) * a.Zp + i] : make_float2(0.f, 0.f);
+            const long long idx = (row0 + r) * a.Zp + i;
+            tile[r * PZ + i] = (r < nr && EVX_IN(idx, a.nrows * a.Zp)) ? a.in[idx] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         // C2R pre-processing: Z[k] = (X_k + conj X_{M-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{M-k});
@@ -260,7 +283,7 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
         const double cbd = a.cbar ? *a.cbar : 0.0;
         const float cb = (float)cbd;
         const float cbl = (float)(cbd - (double)cb);
-        const float gp = (float)(3.0 * cbd * cbd - 1.0);  // g'(cbar)
+        const float gp = a.nl_only ? 0.f : (float)(3.0 * cbd * cbd - 1.0);  // g'(cbar); 0: remainder N only
         const float c3 = (float)(3.0 * cbd);
         const float s = a.scale;
         double acc = 0.0;
@@ -268,13 +291,15 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
             const int r = e / M, n = e - r * M;
             const float2 z = tile[r * PZ + n];
             if (MODE == Z_ADJ) {
-                const float2 cn = reinterpret_cast<const float2*>(a.cn + (row0 + r) * a.cnpitch)[n];
+                const float2 cn = EVX_IN((row0 + r) * a.cnpitch + 2 * n + 1, a.nrows * a.cnpitch)
+                                      ? reinterpret_cast<const float2*>(a.cn + (row0 + r) * a.cnpitch)[n]
+                                      : make_float2(0.f, 0.f);
                 const float d0 = fmaf(3.f * cn.x, cn.x, -1.f), d1 = fmaf(3.f * cn.y, cn.y, -1.f);
                 tile[r * PZ + n] = make_float2(z.x * s * d0, z.y * s * d1);
             } else {
                 const float c0 = fmaf(z.x, s, cbl) + cb, c1 = fmaf(z.y, s, cbl) + cb;
                 if (MODE == Z_STEP) {
-                    if (a.rout)
+                    if (a.rout && EVX_IN((row0 + r) * a.rpitch + 2 * n + 1, a.nrows * a.rpitch))
                         reinterpret_cast<float2*>(a.rout + (row0 + r) * a.rpitch)[n] = make_float2(c0, c1);
                     // g(c) - g(cbar) from d = c - cbar (see the fast z pass)
                     const float d0 = z.x * s, d1 = z.y * s;
@@ -283,7 +308,7 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
                     if (a.gsum) acc += (double)gv.x + (double)gv.y;
                 } else {  // Z_C2R
                     const long long rr = a.map_rows ? user_row(row0 + r, a.YB, a.nxr, a.nyr) : row0 + r;
-                    if (a.rout) {
+                    if (a.rout && EVX_IN(rr * a.rpitch + 2 * n + 1, a.nrows * a.rpitch)) {
                         float2* o = reinterpret_cast<float2*>(a.rout + rr * a.rpitch) + n;
                         if (a.accumulate) {  // the variable-mobility step adds its increment
                             const float2 prev = *o;
@@ -337,7 +362,8 @@ __global__ void __launch_bounds__(NT, 2) zpass_kernel(ZPassArgs a) {
     __syncthreads();
     for (int e = threadIdx.x; e < nr * (M + 1); e += NT) {
         const int r = e / (M + 1), i = e - r * (M + 1);
-        a.out[(row0 + r) * a.Zp + i] = tile[r * PZ + i];
+        const long long idx = (row0 + r) * a.Zp + i;
+        if (EVX_IN(idx, a.nrows * a.Zp)) a.out[idx] = tile[r * PZ + i];
     }
 }
 
@@ -349,7 +375,8 @@ __global__ void __launch_bounds__(NT) sum_rows_kernel(const float* c, long long 
     double acc = 0.0;
     for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
         const float* row = c + r * pitch;
-        for (int z = threadIdx.x; z < rowlen; z += NT) acc += (double)row[z];
+        for (int z = threadIdx.x; z < rowlen; z += NT)
+            if (EVX_IN(r * pitch + z, nrows * pitch)) acc += (double)row[z];
     }
     acc = block_sum_double(acc, ws);
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -412,6 +439,11 @@ __device__ __forceinline__ VmRow vm_row(long long row, int nx, int ny, int nz) {
     return r;
 }
 
+// checked load of a real field of n values (the bounds-checked build tests i)
+__device__ __forceinline__ float ldf(const float* __restrict__ p, long long i, long long n) {
+    return EVX_IN(i, n) ? p[i] : 0.f;
+}
+
 // mu = c^3 - c - (kappa / h^2) (sum of the 6 neighbours - 6 c)
 __global__ void __launch_bounds__(256) vm_mu_kernel(const float* __restrict__ c, float* __restrict__ mu, int nx,
                                                      int ny, int nz, float kh2) {
@@ -420,10 +452,11 @@ __global__ void __launch_bounds__(256) vm_mu_kernel(const float* __restrict__ c,
         const VmRow r = vm_row(row, nx, ny, nz);
         for (int z = threadIdx.x; z < nz; z += blockDim.x) {
             const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
-            const float v = c[r.base + z];
-            const float nb = ((c[r.xp + z] + c[r.xm + z]) + (c[r.yp + z] + c[r.ym + z])) +
-                             (c[r.base + zp] + c[r.base + zm]);
-            mu[r.base + z] = v * (v * v - 1.f) - kh2 * fmaf(-6.f, v, nb);
+            const long long V = nrows * nz;
+            const float v = ldf(c, r.base + z, V);
+            const float nb = ((ldf(c, r.xp + z, V) + ldf(c, r.xm + z, V)) + (ldf(c, r.yp + z, V) + ldf(c, r.ym + z, V))) +
+                             (ldf(c, r.base + zp, V) + ldf(c, r.base + zm, V));
+            if (EVX_IN(r.base + z, V)) mu[r.base + z] = v * (v * v - 1.f) - kh2 * fmaf(-6.f, v, nb);
         }
     }
 }
@@ -439,11 +472,12 @@ __global__ void __launch_bounds__(256) vm_rhs_kernel(const float* __restrict__ c
         for (int z = threadIdx.x; z < nz; z += blockDim.x) {
             const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;
             const long long idx[6] = {r.xp + z, r.xm + z, r.yp + z, r.ym + z, r.base + zp, r.base + zm};
-            const float mi = mob(c[r.base + z]), ui = mu[r.base + z];
+            const long long V = nrows * nz;
+            const float mi = mob(ldf(c, r.base + z, V)), ui = ldf(mu, r.base + z, V);
             float acc = 0.f;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) acc = fmaf(0.5f * (mi + mob(c[idx[q]])), mu[idx[q]] - ui, acc);
-            rhs[r.base + z] = acc * ih2;
+            for (int q = 0; q < 6; ++q) acc = fmaf(0.5f * (mi + mob(ldf(c, idx[q], V))), ldf(mu, idx[q], V) - ui, acc);
+            if (EVX_IN(r.base + z, V)) rhs[r.base + z] = acc * ih2;
         }
     }
 }
@@ -458,9 +492,10 @@ __global__ void __launch_bounds__(256) vm_energy_kernel(const float* __restrict_
         const VmRow r = vm_row(row, nx, ny, nz);
         for (int z = threadIdx.x; z < nz; z += blockDim.x) {
             const int zp = z + 1 == nz ? 0 : z + 1;
-            const double v = c[r.base + z];
+            const long long V = nrows * nz;
+            const double v = ldf(c, r.base + z, V);
             const double q = v * v - 1.0;
-            const double dx = c[r.xp + z] - v, dy = c[r.yp + z] - v, dz = c[r.base + zp] - v;
+            const double dx = ldf(c, r.xp + z, V) - v, dy = ldf(c, r.yp + z, V) - v, dz = ldf(c, r.base + zp, V) - v;
             acc += 0.25 * q * q + k2h2 * (dx * dx + dy * dy + dz * dz);
         }
     }
@@ -499,6 +534,21 @@ template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int bounds_line_kernels(bool clear) {
+#ifdef EVX_BOUNDS_CHECK
+    int h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_bounds_line, sizeof(int)) != cudaSuccess) return -1;
+    if (clear && h) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_bounds_line, &z, sizeof(int));
+    }
+    return h;
+#else
+    (void)clear;
+    return 0;
+#endif
 }
 
 bool fast_paths_enabled() {
@@ -552,7 +602,9 @@ int zpass_grid(const ZPassArgs& a) {
 
 cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st, int* grid_used) {
     cudaError_t fe;
-    if (mode == Z_STEP && !a.generic && fast_paths_enabled() && fast_zstep(a, st, &fe, grid_used)) return fe;
+    if ((mode == Z_STEP || mode == Z_ADJ) && !a.generic && fast_paths_enabled() &&
+        fast_zstep(a, st, &fe, grid_used, mode == Z_ADJ))
+        return fe;
     if ((mode == Z_R2C || mode == Z_C2R) && a.fast_ok && !a.generic && fast_paths_enabled() &&
         fast_zconv(a, mode == Z_R2C ? -1 : 1, st, &fe, grid_used))
         return fe;

@@ -283,16 +283,60 @@ __global__ void sample_sum_kernel(const float* f, long long V, double* partials,
 
 // out = base + (d - mean_s(d)) per sample (base may be null: out = d - mean)
 __global__ void zero_mean_add_kernel(const float* base, const float* d, const double* partials, int nb, long long V,
-                                     float* out) {
+                                     float* out, const double* scale) {
     const int s = blockIdx.y;
     double m = 0.0;
     for (int b = 0; b < nb; ++b) m += partials[s * nb + b];
     const float mean = (float)(m / (double)V);
+    const float f = scale ? (float)scale[s] : 1.f;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V;
          v += (long long)gridDim.x * blockDim.x) {
-        const float x = d[s * V + v] - mean;
+        const float x = f * (d[s * V + v] - mean);
         out[s * V + v] = base ? base[s * V + v] + x : x;
     }
+}
+
+// Per sample s and block b: with the sample's FP64 mean m (from the partial sums
+// pm), partial FP64 sums of d^2 and N^2, d = x - m, N = d^2 (3 m + d) (the
+// nonlinear remainder of c^3 - c about the mean): out[(s * 2 + 0|1) * nb + b].
+__global__ void nl_moments_kernel(const float* x, long long V, const double* pm, int nb, double* out) {
+    __shared__ double ws[2][256];
+    const int s = blockIdx.y;
+    double m = 0.0;
+    for (int b = 0; b < nb; ++b) m += pm[s * nb + b];
+    m /= (double)V;
+    double a2 = 0.0, n2 = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const double d = (double)x[s * V + v] - m;
+        const double N = d * d * (3.0 * m + d);
+        a2 += d * d;
+        n2 += N * N;
+    }
+    ws[0][threadIdx.x] = a2;
+    ws[1][threadIdx.x] = n2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ws[0][threadIdx.x] += ws[0][threadIdx.x + o];
+            ws[1][threadIdx.x] += ws[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[(s * 2 + 0) * nb + blockIdx.x] = ws[0][0];
+        out[(s * 2 + 1) * nb + blockIdx.x] = ws[1][0];
+    }
+}
+// scale[s] = min(1, sqrt(sum N^2 / sum d^2)) (0 for a uniform sample), fixed order
+__global__ void nl_scale_kernel(const double* mom, int nb, int nsamples, double* scale) {
+    const int s = threadIdx.x;
+    if (s >= nsamples || blockIdx.x != 0) return;
+    double a2 = 0.0, n2 = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        a2 += mom[(s * 2 + 0) * nb + b];
+        n2 += mom[(s * 2 + 1) * nb + b];
+    }
+    scale[s] = a2 > 0.0 ? fmin(1.0, sqrt(n2 / a2)) : 0.0;
 }
 
 // squared error: partials of sum (p - t)^2 (FP64); grad = scale (p - t)
@@ -305,6 +349,20 @@ __global__ void mse_kernel(const float* p, const float* t, long long n, float sc
         acc += (double)d * d;
         if (grad) grad[i] = scale * d;
     }
+    ws[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) ws[threadIdx.x] += ws[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = ws[0];
+}
+// partials[b] = FP64 sum of |x| over a grid-stride share of the n values
+__global__ void abs_sum_kernel(const float* x, long long n, double* partials) {
+    __shared__ double ws[256];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += fabs((double)x[i]);
     ws[threadIdx.x] = acc;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -663,7 +721,28 @@ evx_status evx_nn_zero_mean_add(const float* base, const float* d, int nsamples,
         return nn_fail(EVX_ERR_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     sample_sum_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(d, V, partials, nparts);
-    zero_mean_add_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(base, d, partials, nparts, V, out);
+    zero_mean_add_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(base, d, partials, nparts, V, out, nullptr);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_zero_mean_add_scaled(const float* base, const float* d, const double* scale, int nsamples, long long V,
+                                       double* partials, int nparts, float* out, void* stream) {
+    if (!d || !out || !partials || !scale || nsamples <= 0 || nparts <= 0 || nparts > 4096)
+        return nn_fail(EVX_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    sample_sum_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(d, V, partials, nparts);
+    zero_mean_add_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(base, d, partials, nparts, V, out, scale);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_nl_scale(const float* c, int nsamples, long long V, double* partials, int nparts, double* scale,
+                           void* stream) {
+    if (!c || !partials || !scale || nsamples <= 0 || nsamples > 32 || V <= 0 || nparts <= 0 || nparts > 4096)
+        return nn_fail(EVX_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    sample_sum_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(c, V, partials, nparts);
+    nl_moments_kernel<<<dim3(nparts, nsamples), 256, 0, st>>>(c, V, partials, nparts, partials + (long long)nsamples * nparts);
+    nl_scale_kernel<<<1, 32, 0, st>>>(partials + (long long)nsamples * nparts, nparts, nsamples, scale);
     return nn_cuda(cudaGetLastError());
 }
 
@@ -672,6 +751,14 @@ evx_status evx_nn_mse(const float* p, const float* t, long long n, float grad_sc
     if (!p || !t || !partials || !d_sum || nparts <= 0) return nn_fail(EVX_ERR_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     mse_kernel<<<nparts, 256, 0, st>>>(p, t, n, grad_scale, grad, partials);
+    sum_partials_kernel<<<1, 32, 0, st>>>(partials, nparts, d_sum);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_abs_sum(const float* x, long long n, double* partials, int nparts, double* d_sum, void* stream) {
+    if (!x || n <= 0 || !partials || !d_sum || nparts <= 0) return nn_fail(EVX_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    abs_sum_kernel<<<nparts, 256, 0, st>>>(x, n, partials);
     sum_partials_kernel<<<1, 32, 0, st>>>(partials, nparts, d_sum);
     return nn_cuda(cudaGetLastError());
 }

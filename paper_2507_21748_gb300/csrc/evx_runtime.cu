@@ -9,12 +9,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "evx_grid_impl.h"
 #include "evx_tables.h"
 
 using namespace evx;
 
 static const int GRAPH_CHUNK = 16;
+
+// NVTX range for the duration of a scope (a no-op unless a profiler is attached);
+// the public calls and, in profiling mode, each pass of a step carry one
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 static thread_local std::string tl_err;
 
 static evx_status fail(evx_grid* g, evx_status s, const char* fmt, ...) {
@@ -189,6 +200,15 @@ evx_status set_error(evx_grid* g, evx_status s, const char* msg) { return fail(g
 using namespace evxrt;
 
 // --------------------------------------------------------- step sequence
+// profiling mode: record event k of a step and move the NVTX range on to the
+// pass that follows it (next = nullptr after the last pass)
+static void mark(cudaEvent_t* ev, int k, cudaStream_t st, const char* next) {
+    if (!ev) return;
+    cudaEventRecord(ev[k], st);
+    if (k > 0) nvtxRangePop();
+    if (next) nvtxRangePushA(next);
+}
+
 // ev: null, or 5 events recorded around the four passes
 // variable mobility: c (real, in S) <- c + F^-1{ dt / (1 + dt M kappa |k|^4) F{div(M(c) grad mu)} }
 // events: [FD stencils] [z R2C] [y forward] [x preconditioner + y inverse + z C2R-add]
@@ -197,11 +217,11 @@ static cudaError_t issue_vm_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) 
     float* c = reinterpret_cast<float*>(g->S);
     float* mu = reinterpret_cast<float*>(g->W);
     const double ih2 = 1.0 / (g->p.h * g->p.h);
-    if (ev) cudaEventRecord(ev[0], st);
+    mark(ev, 0, st, "FD stencils");
     if ((e = launch_vm_mu(c, mu, g->nx, g->ny, g->nz, (float)(g->p.kappa * ih2), st)) != cudaSuccess) return e;
     if ((e = launch_vm_rhs(c, mu, g->R, g->nx, g->ny, g->nz, (float)g->p.M, (float)ih2, st)) != cudaSuccess)
         return e;
-    if (ev) cudaEventRecord(ev[1], st);
+    mark(ev, 1, st, "z R2C");
     ZPassArgs z = z_args(g);
     z.rin = g->R;
     z.rpitch = g->nz;
@@ -209,9 +229,9 @@ static cudaError_t issue_vm_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) 
     z.out = g->W;
     z.fast_ok = 1;
     if ((e = launch_zpass(z, Z_R2C, st)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[2], st);
+    mark(ev, 2, st, "y forward");
     if ((e = launch_spass(y_args(g, g->W, g->W), -1, st)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[3], st);
+    mark(ev, 3, st, "x preconditioner, y inverse, z C2R-add");
     XUpdArgs xa = x_args(g, g->W, g->W, g->W, g->p.dt, g->p.M, g->p.kappa);
     xa.model = 2;
     xa.dtM = (float)g->p.dt;  // preconditioner numerator
@@ -225,14 +245,14 @@ static cudaError_t issue_vm_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) 
     z2.accumulate = 1;
     z2.fast_ok = 1;
     if ((e = launch_zpass(z2, Z_C2R, st)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[4], st);
+    mark(ev, 4, st, nullptr);
     return cudaSuccess;
 }
 
 static cudaError_t issue_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) {
     if (g->model == EVX_MODEL_VM) return issue_vm_step(g, st, ev);
     cudaError_t e;
-    if (ev) cudaEventRecord(ev[0], st);
+    mark(ev, 0, st, g->fused ? "fused y-z-y pass" : "y inverse");
     if (g->fused) {  // y inverse + z step + y forward in one pass (its time is reported as pass 1)
         YZYArgs y = yzy_args(g);
         const bool ac = g->model == EVX_MODEL_AC;
@@ -246,17 +266,17 @@ static cudaError_t issue_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) {
                 return e;
         }
         if (ev) {
-            cudaEventRecord(ev[1], st);
-            cudaEventRecord(ev[2], st);
-            cudaEventRecord(ev[3], st);
+            mark(ev, 1, st, "(in the fused pass)");
+            mark(ev, 2, st, "(in the fused pass)");
+            mark(ev, 3, st, "x pass + update");
         }
         if ((e = launch_xupdate(x_args(g, g->W, g->S, g->S, g->p.dt, g->p.M, g->p.kappa), st)) != cudaSuccess)
             return e;
-        if (ev) cudaEventRecord(ev[4], st);
+        mark(ev, 4, st, nullptr);
         return cudaSuccess;
     }
     if ((e = launch_spass(y_args(g, g->S, g->W), +1, st)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[1], st);
+    mark(ev, 1, st, "z C2R, c^3 - c, R2C");
     ZPassArgs z = z_args(g);
     z.in = g->W;
     z.out = g->W;
@@ -271,13 +291,13 @@ static cudaError_t issue_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) {
         if ((e = launch_ac_mean(g->d_part, zgrid, g->d_scal, g->p.dt * g->p.M, 1.0 / V, st)) != cudaSuccess)
             return e;
     }
-    if (ev) cudaEventRecord(ev[2], st);
+    mark(ev, 2, st, "y forward");
     if ((e = launch_spass(y_args(g, g->W, g->W), -1, st)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[3], st);
+    mark(ev, 3, st, "x pass + update");
     if ((e = launch_xupdate(x_args(g, g->W, g->S, g->S, g->p.dt, g->p.M, g->p.kappa), st)) !=
         cudaSuccess)
         return e;
-    if (ev) cudaEventRecord(ev[4], st);
+    mark(ev, 4, st, nullptr);
     return cudaSuccess;
 }
 
@@ -478,6 +498,7 @@ static evx_status load_real(evx_grid* g, const float* rows, long long pitch, int
 static size_t field_bytes(const evx_grid* g) { return sizeof(float) * (size_t)g->nx * g->ny * g->nz; }
 
 evx_status evx_set_field(evx_grid* g, const float* d_c) {
+    NvtxRange nvtx_("evx_set_field");
     if (!g || !d_c) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!aligned8(d_c)) return fail(g, EVX_ERR_ARG, "field pointer must be 8-byte aligned");
     if (g->model == EVX_MODEL_VM) {  // the variable-mobility state is the real field itself
@@ -510,6 +531,7 @@ static evx_status host_rows_copy(evx_grid* g, float* host, bool to_device) {
 }
 
 evx_status evx_set_field_host(evx_grid* g, const float* h_c) {
+    NvtxRange nvtx_("evx_set_field_host");
     if (!g || !h_c) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (g->model == EVX_MODEL_VM) {
         CK(cudaMemcpyAsync(g->S, h_c, field_bytes(g), cudaMemcpyHostToDevice, g->st));
@@ -547,6 +569,7 @@ static evx_status store_real(evx_grid* g, float* rows, long long pitch, double* 
 }
 
 evx_status evx_get_field(evx_grid* g, float* d_out) {
+    NvtxRange nvtx_("evx_get_field");
     if (!g || !d_out) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     if (!aligned8(d_out)) return fail(g, EVX_ERR_ARG, "output pointer must be 8-byte aligned");
@@ -558,6 +581,7 @@ evx_status evx_get_field(evx_grid* g, float* d_out) {
 }
 
 evx_status evx_get_field_host(evx_grid* g, float* h_out) {
+    NvtxRange nvtx_("evx_get_field_host");
     if (!g || !h_out) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     if (g->model == EVX_MODEL_VM) {
@@ -601,6 +625,7 @@ evx_status evx_ch_step(evx_grid* g, int n_steps) {
 }
 
 evx_status evx_step(evx_grid* g, int n_steps) {
+    NvtxRange nvtx_("evx_step");
     if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
     if (n_steps < 0) return fail(g, EVX_ERR_ARG, "n_steps < 0");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
@@ -620,7 +645,10 @@ evx_status evx_step(evx_grid* g, int n_steps) {
                     }
                 }
             }
-            CK(issue_step(g, g->st, &g->evpool[g->ev_used]));
+            {
+                NvtxRange r_("step (profiled: one launch per pass)");
+                CK(issue_step(g, g->st, &g->evpool[g->ev_used]));
+            }
             g->ev_used += 5;
         }
         return EVX_OK;
@@ -642,6 +670,31 @@ evx_status evx_step(evx_grid* g, int n_steps) {
     return EVX_OK;
 }
 
+evx_status evx_ch_block(evx_grid* g, int n_steps) {
+    NvtxRange nvtx_("evx_ch_block");
+    if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
+    if (g->model != EVX_MODEL_CH) return fail(g, EVX_ERR_STATE, "evx_ch_block is defined for the Cahn-Hilliard model");
+    if (n_steps < 1 || n_steps > 4096) return fail(g, EVX_ERR_ARG, "n_steps must be 1..4096");
+    if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
+    // y inverse, z pass forming N only, y forward, x pass with the block symbols
+    // (the separate passes, also on a grid created with the fused y-z-y pass)
+    CK(launch_spass(y_args(g, g->S, g->W), +1, g->st));
+    ZPassArgs z = z_args(g);
+    z.in = g->W;
+    z.out = g->W;
+    z.cbar = g->d_scal;
+    z.nl_only = 1;
+    CK(launch_zpass(z, Z_STEP, g->st));
+    CK(launch_spass(y_args(g, g->W, g->W), -1, g->st));
+    XUpdArgs xa = x_args(g, g->W, g->S, g->S, g->p.dt, g->p.M, g->p.kappa);
+    xa.model = 3;
+    xa.nblk = n_steps;
+    xa.cbar = g->d_scal;
+    CK(launch_xupdate(xa, g->st));
+    g->steps += n_steps;
+    return EVX_OK;
+}
+
 // variable mobility: FP64 mean of the real field -> d_scal[0]
 static cudaError_t vm_sum(evx_grid* g) {
     const long long nrows = (long long)g->nx * g->ny;
@@ -653,6 +706,7 @@ static cudaError_t vm_sum(evx_grid* g) {
 }
 
 evx_status evx_energy(evx_grid* g, double* E, double* mass) {
+    NvtxRange nvtx_("evx_energy");
     if (!g) return fail(g, EVX_ERR_ARG, "grid is NULL");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     const double h3 = g->p.h * g->p.h * g->p.h;
@@ -768,6 +822,22 @@ evx_status evx_pass_bytes(const evx_grid* g, int pass, double* bytes) {
     return EVX_OK;
 }
 
+evx_status evx_debug_bounds(int* enabled, int* line) {
+#ifdef EVX_BOUNDS_CHECK
+    const int on = 1;
+#else
+    const int on = 0;
+#endif
+    if (enabled) *enabled = on;
+    if (line) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail(nullptr, EVX_ERR_CUDA, "synchronise: %s", cudaGetErrorString(e));
+        const int a = bounds_line_kernels(true), b = bounds_line_adjoint(true);
+        *line = a ? a : b;
+    }
+    return EVX_OK;
+}
+
 evx_status evx_step_count(const evx_grid* g, long long* steps) {
     if (!g || !steps) return fail(nullptr, EVX_ERR_ARG, "NULL argument");
     *steps = g->steps;
@@ -810,6 +880,7 @@ size_t state_bytes(const evx_grid* g) {
 extern "C" {
 
 evx_status evx_save(evx_grid* g, const char* path) {
+    NvtxRange nvtx_("evx_save");
     if (!g || !path) return fail(g, EVX_ERR_ARG, "NULL argument");
     if (!g->has_field) return fail(g, EVX_ERR_STATE, "no field set");
     CK(cudaStreamSynchronize(g->st));
@@ -856,6 +927,7 @@ evx_status evx_save(evx_grid* g, const char* path) {
 }
 
 evx_status evx_load(evx_grid* g, const char* path) {
+    NvtxRange nvtx_("evx_load");
     if (!g || !path) return fail(g, EVX_ERR_ARG, "NULL argument");
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(g, EVX_ERR_IO, "cannot open %s", path);

@@ -11,7 +11,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libevx.so")
+# EVX_LIB selects another build of the same library (the bounds-checked
+# libevx_bounds.so of the debug tests); default: the normal build
+LIB_PATH = os.environ.get("EVX_LIB") or os.path.join(_HERE, "_lib", "libevx.so")
 
 (EVX_OK, EVX_ERR_ARG, EVX_ERR_SIZE, EVX_ERR_OOM, EVX_ERR_CUDA, EVX_ERR_NONFINITE, EVX_ERR_STATE,
  EVX_ERR_IO) = range(8)
@@ -21,10 +23,10 @@ STATUS_NAMES = ["EVX_OK", "EVX_ERR_ARG", "EVX_ERR_SIZE", "EVX_ERR_OOM", "EVX_ERR
 # every entry point declared in include/evx.h
 EXPORTS = [
     "evx_grid_create", "evx_grid_destroy", "evx_set_params", "evx_get_params", "evx_set_stream", "evx_set_field",
-    "evx_set_field_host", "evx_get_field", "evx_get_field_host", "evx_ch_step", "evx_energy",
+    "evx_set_field_host", "evx_get_field", "evx_get_field_host", "evx_ch_step", "evx_ch_block", "evx_energy",
     "evx_mean", "evx_ch_adjoint", "evx_footprint", "evx_set_profiling", "evx_pass_times",
     "evx_pass_bytes", "evx_ch_step_static", "evx_set_model", "evx_get_model", "evx_step", "evx_step_count",
-    "evx_save", "evx_load", "evx_last_error",
+    "evx_save", "evx_load", "evx_debug_bounds", "evx_last_error",
 ]
 MODELS = {"ch": 0, "ac": 1, "vm": 2}  # evx_model: Cahn-Hilliard, Allen-Cahn, variable-mobility CH
 
@@ -58,6 +60,7 @@ def _load():
         "evx_get_field": ([vp, fp], st),
         "evx_get_field_host": ([vp, fp], st),
         "evx_ch_step": ([vp, i], st),
+        "evx_ch_block": ([vp, i], st),
         "evx_energy": ([vp, dp, dp], st),
         "evx_mean": ([vp, dp], st),
         "evx_ch_adjoint": ([vp, fp, i, i, fp, fp, dp, dp], st),
@@ -72,6 +75,7 @@ def _load():
         "evx_step_count": ([vp, ctypes.POINTER(ctypes.c_longlong)], st),
         "evx_save": ([vp, ctypes.c_char_p], st),
         "evx_load": ([vp, ctypes.c_char_p], st),
+        "evx_debug_bounds": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], st),
         "evx_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -197,6 +201,10 @@ class Grid:
         self._ck(lib.evx_get_params(self._h, ctypes.byref(p)))
         self.params = p
 
+    def block(self, n=10):
+        """One block of n steps: linear part exact, nonlinear remainder frozen (evx_ch_block)."""
+        self._ck(lib.evx_ch_block(self._h, int(n)))
+
     def energy(self):
         E = ctypes.c_double()
         m = ctypes.c_double()
@@ -240,6 +248,17 @@ class Grid:
                                     ctypes.c_void_p(dLdc0.data_ptr()), ctypes.byref(gk),
                                     ctypes.byref(gm)))
         return dLdc0, gk.value, gm.value
+
+
+def debug_bounds():
+    """(enabled, line): whether this is the bounds-checked build, and the source line
+    of the first out-of-bounds access the checked kernels skipped since the last
+    call (0 if none). Synchronises the device."""
+    en, line = ctypes.c_int(), ctypes.c_int()
+    s = lib.evx_debug_bounds(ctypes.byref(en), ctypes.byref(line))
+    if s != EVX_OK:
+        raise EvxError(s, lib.evx_last_error(None).decode())
+    return en.value, line.value
 
 
 def ch_step_static(c_in, c_out, n_steps, dt=0.1, M=1.0, kappa=1.0, h=1.0, stream=None):

@@ -18,8 +18,8 @@ lib = evx.lib
 NN_EXPORTS = ["evx_nn_conv3d", "evx_nn_conv3d_wgrad", "evx_nn_bias_grad", "evx_nn_flip_weights",
               "evx_nn_field_to_act", "evx_nn_zero_mean_add", "evx_nn_mse", "evx_nn_adam",
               "evx_nn_f32_to_bf16", "evx_nn_set_conv_engine", "evx_nn_conv_engine", "evx_nn_check",
-              "evx_nn_lift", "evx_nn_project",
-              "evx_nn_last_error"]
+              "evx_nn_lift", "evx_nn_project", "evx_nn_abs_sum", "evx_nn_zero_mean_add_scaled",
+              "evx_nn_nl_scale", "evx_nn_last_error"]
 EPI_PLAIN, EPI_GELU, EPI_RESID, EPI_GELU_BWD, EPI_FIELD = range(5)
 ENGINE_TCGEN05, ENGINE_MMA_SYNC = 0, 1
 
@@ -34,6 +34,9 @@ def _setup():
         "evx_nn_field_to_act": [vp, ll, i, f, vp, vp],
         "evx_nn_zero_mean_add": [vp, vp, i, ll, vp, i, vp, vp],
         "evx_nn_mse": [vp, vp, ll, f, vp, vp, i, vp, vp],
+        "evx_nn_abs_sum": [vp, ll, vp, i, vp, vp],
+        "evx_nn_zero_mean_add_scaled": [vp, vp, vp, i, ll, vp, i, vp, vp],
+        "evx_nn_nl_scale": [vp, i, ll, vp, i, vp, vp],
         "evx_nn_adam": [vp, vp, vp, vp, i, f, f, f, f, i, vp, vp],
         "evx_nn_f32_to_bf16": [vp, i, vp, vp],
         "evx_nn_set_conv_engine": [i],
@@ -90,7 +93,7 @@ class Net:
     CIN = 16  # the input field is padded to 16 channels (channel 0 = c)
     CPROJ = 16  # the projection writes 16 channels, channel 0 is used
 
-    def __init__(self, shape, batch, width=32, nblocks=4, seed=0, train=True):
+    def __init__(self, shape, batch, width=32, nblocks=4, seed=0, train=True, proj_gain=0.01):
         assert width == 32
         self.shape, self.batch, self.W, self.nb = tuple(shape), int(batch), width, nblocks
         self.training = train
@@ -107,7 +110,7 @@ class Net:
         for k in range(nblocks):
             init += [("W1_%d" % k, w(W, W, 27 * W, 1.0)), ("b1_%d" % k, np.zeros(W, np.float32)),
                      ("W2_%d" % k, w(W, W, 27 * W, 0.1)), ("b2_%d" % k, np.zeros(W, np.float32))]
-        wp = w(self.CPROJ, W, 27 * W, 0.01)
+        wp = w(self.CPROJ, W, 27 * W, proj_gain)
         wp[:, 1:, :] = 0.0  # only channel 0 of the projection reaches the output
         init += [("Wp", wp), ("bp", np.zeros(self.CPROJ, np.float32))]
         w0 = init[0][1]
@@ -123,6 +126,9 @@ class Net:
                       for n, t in self.p.items() if n.startswith("W") and n != "W0"}
         self.step_count = 0
         self._refresh_bf16()
+        # output scale of the base-corrected form (evx_nn_nl_scale), per sample
+        self.scale = torch.zeros(self.batch, dtype=torch.float64, device=dev)
+        self._scaled = False
         bf = torch.bfloat16
         nv = self.nvox
         # the padded lift input: for the lift's weight gradient, or for the tensor-core lift when W != 32
@@ -136,6 +142,7 @@ class Net:
             sms = torch.cuda.get_device_properties(0).multi_processor_count
             self.nparts = 2 * sms
             self.dpart = torch.empty(self.nparts * max(W, self.batch), dtype=torch.float64, device=dev)
+            self.spart = torch.empty(3 * self.nparts * self.batch, dtype=torch.float64, device=dev)
             return
         self.h = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks + 1)]
         self.u = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks)]
@@ -151,6 +158,7 @@ class Net:
         self.wpart = torch.empty(self.partial_floats, dtype=torch.float32, device=dev)
         self.nparts = 2 * sms
         self.dpart = torch.empty(self.nparts * max(W, self.batch), dtype=torch.float64, device=dev)
+        self.spart = torch.empty(3 * self.nparts * self.batch, dtype=torch.float64, device=dev)
         self.dsum = torch.zeros(1, dtype=torch.float64, device=dev)
 
     # ---------------------------------------------------------- parameters
@@ -197,9 +205,14 @@ class Net:
                                  _stream()))
 
     # -------------------------------------------------------------- forward
-    def forward(self, c):
-        """c: float32 CUDA tensor (batch, X, Y, Z) -> c + zero-mean correction."""
+    def forward(self, c, base=None):
+        """c: float32 CUDA tensor (batch, X, Y, Z) -> base + zero-mean correction,
+        with base = c (the network predicts the whole block's increment) or the
+        block propagator's prediction of the same block (the network predicts its
+        error; see block_base)."""
         assert c.is_contiguous() and c.numel() == self.nvox and c.dtype == torch.float32
+        if base is not None:
+            assert base.is_contiguous() and base.shape == c.shape and base.dtype == torch.float32
         self._c = c
         s = _stream()
         W = self.W
@@ -222,8 +235,14 @@ class Net:
                                    _p(self.d), self.batch, X, Y, Z, s))
         else:
             self._conv(self.h[self.nb], "Wp", self.p["bp"], self.d, W, self.CPROJ, EPI_FIELD)
-        _ck(lib.evx_nn_zero_mean_add(_p(c), _p(self.d), self.batch, self.V, _p(self.dpart), self.nparts,
-                                     _p(self.pred), s))
+        self._scaled = base is not None
+        if base is None:  # c + zero-mean correction
+            _ck(lib.evx_nn_zero_mean_add(_p(c), _p(self.d), self.batch, self.V, _p(self.dpart), self.nparts,
+                                         _p(self.pred), s))
+        else:  # base + scale * zero-mean correction, scale = the nonlinearity's relative strength
+            _ck(lib.evx_nn_nl_scale(_p(c), self.batch, self.V, _p(self.spart), self.nparts, _p(self.scale), s))
+            _ck(lib.evx_nn_zero_mean_add_scaled(_p(base), _p(self.d), _p(self.scale), self.batch, self.V,
+                                                _p(self.dpart), self.nparts, _p(self.pred), s))
         return self.pred.view(c.shape)
 
     # ------------------------------------------------------------- backward
@@ -240,9 +259,13 @@ class Net:
         W = self.W
         _ck(lib.evx_nn_mse(_p(self.pred), _p(target), self.nvox, 2.0 / self.nvox, _p(self.gpred),
                            _p(self.dpart), self.nparts, _p(self.dsum), s))
-        # transpose of the zero-mean projection is the projection itself
-        _ck(lib.evx_nn_zero_mean_add(None, _p(self.gpred), self.batch, self.V, _p(self.dpart), self.nparts,
-                                     _p(self.gpred), s))
+        # transpose of the (scaled) zero-mean projection is the projection itself
+        if self._scaled:
+            _ck(lib.evx_nn_zero_mean_add_scaled(None, _p(self.gpred), _p(self.scale), self.batch, self.V,
+                                                _p(self.dpart), self.nparts, _p(self.gpred), s))
+        else:
+            _ck(lib.evx_nn_zero_mean_add(None, _p(self.gpred), self.batch, self.V, _p(self.dpart), self.nparts,
+                                         _p(self.gpred), s))
         _ck(lib.evx_nn_field_to_act(_p(self.gpred), self.nvox, self.CPROJ, 1.0, _p(self.gact), s))
         self._wgrad(self.gact, self.h[self.nb], "Wp", W, self.CPROJ)
         self._bgrad(self.gact, "bp", self.CPROJ)
@@ -267,20 +290,36 @@ class Net:
         self._refresh_bf16()
 
 
+# ------------------------------------------------------------ base propagator
+def block_base(grid, c, out, block=10):
+    """The block propagator's prediction of c after `block` steps (evx_ch_block:
+    the scheme's linear part exact over the block, its nonlinear remainder
+    N = d^2 (3 cbar + d) frozen at the block's start; one step's cost). grid: an
+    evx.Grid of c's shape and the scheme's parameters; c, out: (X, Y, Z) float32."""
+    grid.set_field(c)
+    grid.block(block)
+    grid.get_field(out)
+
+
 # ----------------------------------------------------------------- training
 class TrajectoryPool:
     """B solver trajectories at `shape`, advanced `block` steps per draw; each
     starts from c0 = mean(seed) + U(-0.05, 0.05) and is restarted with the next
-    seed after `horizon` steps (seeds cycle through first_seed .. last_seed)."""
+    seed after `horizon` steps (seeds cycle through first_seed .. last_seed).
+    With base=True each draw also returns the block propagator's prediction of
+    the block (block_base)."""
 
-    def __init__(self, shape, batch, block=10, horizon=300, seeds=range(256), dt=0.1, M=1.0, kappa=1.0):
+    def __init__(self, shape, batch, block=10, horizon=300, seeds=range(256), dt=0.1, M=1.0, kappa=1.0,
+                 base=False):
         self.shape, self.batch, self.block, self.horizon = tuple(shape), batch, block, horizon
         self.seeds = list(seeds)
         self.next_seed = 0
         self.grids = [evx.Grid(shape, dt=dt, M=M, kappa=kappa) for _ in range(batch)]
+        self.bgrid = evx.Grid(shape, dt=dt, M=M, kappa=kappa) if base else None
         self.age = [0] * batch
         self.cur = torch.empty((batch,) + self.shape, dtype=torch.float32, device="cuda")
         self.nxt = torch.empty_like(self.cur)
+        self.bas = torch.empty_like(self.cur) if base else None
         for i in range(batch):
             self._restart(i)
 
@@ -292,27 +331,33 @@ class TrajectoryPool:
         self.age[i] = 0
 
     def draw(self):
-        """(c_n, c_{n+block}) for every trajectory of the pool."""
+        """(c_n, c_{n+block}) for every trajectory of the pool, and the block
+        propagator's c_{n+block} when the pool was made with base=True."""
         for i, g in enumerate(self.grids):
             if self.age[i] >= self.horizon:
                 self._restart(i)
             g.get_field(self.cur[i])
+            if self.bgrid is not None:
+                block_base(self.bgrid, self.cur[i], self.bas[i], self.block)
             g.step(self.block)
             g.get_field(self.nxt[i])
             self.age[i] += self.block
-        return self.cur, self.nxt
+        return (self.cur, self.nxt) if self.bgrid is None else (self.cur, self.nxt, self.bas)
 
     def close(self):
         for g in self.grids:
             g.close()
+        if self.bgrid is not None:
+            self.bgrid.close()
 
 
 def train(net, pool, iters, lr=2e-3, lr_final=2e-4, log_every=50, log=None):
     """Adam with a geometric learning-rate decay; returns the loss history."""
     hist = []
     for it in range(iters):
-        x, y = pool.draw()
-        net.forward(x.contiguous())
+        batch = pool.draw()
+        x, y = batch[0], batch[1]
+        net.forward(x.contiguous(), batch[2].contiguous() if len(batch) > 2 else None)
         L = net.backward(y.contiguous())
         frac = it / max(iters - 1, 1)
         net.adam(lr * (lr_final / lr) ** frac)
@@ -323,22 +368,38 @@ def train(net, pool, iters, lr=2e-3, lr_final=2e-4, log_every=50, log=None):
 
 
 # -------------------------------------------------------- guarded rollout
-def rollout(net, c0, nblocks, block=10, dt=0.1, M=1.0, kappa=1.0, mass_tol=1e-6, energy_tol=1e-7):
+def rollout(net, c0, nblocks, block=10, dt=0.1, M=1.0, kappa=1.0, mass_tol=1e-6, energy_tol=1e-7, base=False):
     """Advance c0 (batch, X, Y, Z) by nblocks x block steps with the surrogate;
     a sample whose predicted block drifts in mass beyond mass_tol (relative
     to its L1 norm) or raises the energy beyond energy_tol (relative) is
-    recomputed by the plain solver for that block. Returns (fields, stats)."""
+    recomputed by the plain solver for that block. With base=True the network
+    corrects the block propagator's prediction (block_base). Returns (fields, stats)."""
     shape = tuple(c0.shape[1:])
     B = c0.shape[0]
     referee = evx.Grid(shape, dt=dt, M=M, kappa=kappa)
     c = c0.clone()
+    bas = torch.empty_like(c) if base else None
+    nparts = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    l1parts = torch.empty(nparts, dtype=torch.float64, device="cuda")
+    l1sum = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def l1(x):  # FP64 sum of |x| in the library
+        _ck(lib.evx_nn_abs_sum(_p(x), x.numel(), _p(l1parts), nparts, _p(l1sum), _stream()))
+        return float(l1sum.item())
+
     fallbacks = 0
-    t_net = t_guard = t_fb = 0.0
+    t_net = t_guard = t_fb = t_base = 0.0
     E_prev = [None] * B  # refereed energy and mass of each sample's current field
     for _ in range(nblocks):
         torch.cuda.synchronize()
+        tb = time.perf_counter()
+        if base:
+            for i in range(B):
+                block_base(referee, c[i], bas[i], block)
+            torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pred = net.forward(c.contiguous()).clone()
+        t_base += t0 - tb
+        pred = (net.forward(c.contiguous(), bas) if base else net.forward(c.contiguous())).clone()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         t_net += t1 - t0
@@ -347,10 +408,10 @@ def rollout(net, c0, nblocks, block=10, dt=0.1, M=1.0, kappa=1.0, mass_tol=1e-6,
                 referee.set_field(c[i])
                 E_prev[i] = referee.energy()
             E0, m0 = E_prev[i]
-            l1 = float(c[i].abs().double().sum())
+            l1n = l1(c[i])
             referee.set_field(pred[i])
             E1, m1 = referee.energy()
-            ok = abs(m1 - m0) <= mass_tol * l1 and E1 <= E0 * (1 + energy_tol) + 1e-300
+            ok = abs(m1 - m0) <= mass_tol * l1n and E1 <= E0 * (1 + energy_tol) + 1e-300
             E_prev[i] = (E1, m1)
             t2 = time.perf_counter()
             if not ok:
@@ -365,7 +426,22 @@ def rollout(net, c0, nblocks, block=10, dt=0.1, M=1.0, kappa=1.0, mass_tol=1e-6,
         c = pred
     referee.close()
     return c, {"fallbacks": fallbacks, "blocks": nblocks * B, "t_net_s": t_net, "t_guard_s": t_guard - t_fb,
-               "t_fallback_s": t_fb}
+               "t_fallback_s": t_fb, "t_base_s": t_base}
+
+
+def base_rollout(c0, nblocks, block=10, dt=0.1, M=1.0, kappa=1.0):
+    """The block propagator alone (no network, no guard): the method without the
+    learned correction."""
+    shape = tuple(c0.shape[1:])
+    g = evx.Grid(shape, dt=dt, M=M, kappa=kappa)
+    out = torch.empty_like(c0)
+    for i in range(c0.shape[0]):
+        g.set_field(c0[i].contiguous())
+        for _ in range(nblocks):
+            g.block(block)
+        g.get_field(out[i])
+    g.close()
+    return out
 
 
 def solver_run(c0, nsteps, dt=0.1, M=1.0, kappa=1.0):

@@ -318,3 +318,35 @@ def test_guarded_rollout_accepts_the_solver_itself(S):
     c0 = torch.stack([torch.from_numpy(inputs.uniform_field(shape, seed=s)) for s in range(B)]).cuda()
     out, st = S.rollout(Exact(), c0, nblocks=2)
     assert st["fallbacks"] == 0
+
+
+def test_nonlinearity_scale_and_scaled_zero_mean_add(S):
+    """evx_nn_nl_scale against its definition in FP64 (scale = min(1, ||N|| / ||d||),
+    d = c - mean c, N = d^2 (3 mean + d)), and the scaled zero-mean correction."""
+    import torch
+    rng = np.random.default_rng(7)
+    B, V = 3, 4096
+    c = np.stack([0.2 + 0.05 * rng.standard_normal(V), -0.1 + 0.6 * rng.standard_normal(V),
+                  np.full(V, 0.4)]).astype(np.float32)
+    cd = torch.from_numpy(c).cuda()
+    nparts = 8
+    parts = torch.empty(3 * B * nparts, dtype=torch.float64, device="cuda")
+    scale = torch.empty(B, dtype=torch.float64, device="cuda")
+    S._ck(S.lib.evx_nn_nl_scale(S._p(cd), B, V, S._p(parts), nparts, S._p(scale), S._stream()))
+    want = []
+    for s in range(B):
+        x = c[s].astype(np.float64)
+        d = x - x.mean()
+        N = d * d * (3 * x.mean() + d)
+        want.append(min(1.0, float(np.sqrt((N * N).sum() / (d * d).sum()))) if (d * d).sum() > 0 else 0.0)
+    got = scale.cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-12), (got, want)
+    base = torch.from_numpy(rng.standard_normal((B, V)).astype(np.float32)).cuda()
+    dd = torch.from_numpy(rng.standard_normal((B, V)).astype(np.float32)).cuda()
+    out = torch.empty_like(base)
+    dparts = torch.empty(B * nparts, dtype=torch.float64, device="cuda")
+    S._ck(S.lib.evx_nn_zero_mean_add_scaled(S._p(base), S._p(dd), S._p(scale), B, V, S._p(dparts), nparts,
+                                             S._p(out), S._stream()))
+    dn = dd.cpu().numpy().astype(np.float64)
+    ref = base.cpu().numpy() + np.array(want)[:, None] * (dn - dn.mean(axis=1, keepdims=True))
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-5

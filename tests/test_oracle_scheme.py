@@ -162,3 +162,42 @@ def test_step_modes_matches_full_step():
     got = O.step_modes(c, modes, dt, M, kappa, h)
     for i, (a, b, d) in enumerate(modes):
         assert abs(got[i] - full[a, b, d]) < 1e-11
+
+
+def test_block_step_of_one_step_is_the_scheme():
+    """The block propagator with n = 1 is one step of the scheme (the split
+    g = g(cbar) + g'(cbar) d + N(d) is exact and g(cbar) only feeds k = 0)."""
+    c = inputs.uniform_field((16, 12, 10), seed=5, offset=0.2, lo=-0.6, hi=0.6)
+    for h in (1.0, 0.8):
+        a = O.ch_step(c, 0.1, 0.7, 1.3, h, 1)
+        b = O.ch_block_step(c, 0.1, 0.7, 1.3, h, 1)
+        assert np.abs(a - b).max() < 1e-13
+
+
+def test_block_step_linear_regime_and_cosine_closed_form():
+    """A tiny mode on cbar follows L(k)^n exactly up to O(eps^2); a cosine mode's
+    block has the closed form from N = d^2 (3 cbar + d) of d = A cos(t):
+    3 cbar A^2/2 (1 + cos 2t) + (3A^3/4) cos t + (A^3/4) cos 3t, each mode of N
+    multiplied by B S_n with S_n = sum_{j<n} L^j."""
+    N, dt, M, kappa, cbar, n = 32, 0.1, 0.9, 1.1, 0.25, 10
+    x = np.indices((N, N, N)).astype(np.float64)
+    mvec = (2, 1, 0)
+    theta = 2 * np.pi * sum(mvec[d] * x[d] for d in range(3)) / N
+
+    def LBS(mult):
+        k2 = sum((2 * np.pi * mult * m / N) ** 2 for m in mvec)
+        D = 1 + dt * M * kappa * k2 * k2
+        L = (1 - dt * M * k2 * (3 * cbar * cbar - 1)) / D
+        return L, -dt * M * k2 / D, sum(L ** j for j in range(n))
+
+    A = 0.3
+    c = cbar + A * np.cos(theta)
+    (L1, B1, S1), (L2, B2, S2), (L3, B3, S3) = LBS(1), LBS(2), LBS(3)
+    expect = (cbar + (L1 ** n * A + B1 * S1 * 0.75 * A ** 3) * np.cos(theta)
+              + B2 * S2 * 1.5 * cbar * A * A * np.cos(2 * theta) + B3 * S3 * 0.25 * A ** 3 * np.cos(3 * theta))
+    got = O.ch_block_step(c, dt, M, kappa, 1.0, n)
+    assert np.abs(got - expect).max() < 1e-13
+    eps = 1e-7
+    c = cbar + eps * np.cos(theta)
+    got = O.ch_block_step(c, dt, M, kappa, 1.0, n) - cbar
+    assert np.abs(got - L1 ** n * eps * np.cos(theta)).max() < 20 * eps * eps  # the O(eps^2) of N

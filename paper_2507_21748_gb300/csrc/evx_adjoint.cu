@@ -205,6 +205,7 @@ struct AdjStore {
     std::vector<float2*> Sn;   // S_{j+1} for j < K
     float2* Lam = nullptr;
     float2* P = nullptr;
+    float2* seg0 = nullptr;    // start state of the segment being replayed (the captured graph's input)
     double* part = nullptr;
     double* d_acc = nullptr;   // [0] dL/dkappa, [1] dL/dM
     size_t bytes = 0;
@@ -221,6 +222,7 @@ void adjoint_free(evx_grid* g) {
     for (auto p : s->Sn) cudaFree(p);
     if (s->Lam) cudaFree(s->Lam);
     if (s->P) cudaFree(s->P);
+    if (s->seg0) cudaFree(s->seg0);
     if (s->part) cudaFree(s->part);
     if (s->d_acc) cudaFree(s->d_acc);
     g->bytes -= s->bytes;
@@ -266,7 +268,7 @@ static evx_status adj_alloc(evx_grid* g, int K, int nseg) {
     for (int i = 0; i < K && ok; ++i)
         ok = get((void**)&s->cs[i], freal) && get((void**)&s->G[i], fspec) &&
              get((void**)&s->Sn[i], fspec);
-    ok = ok && get((void**)&s->Lam, fspec) && get((void**)&s->P, fspec) &&
+    ok = ok && get((void**)&s->Lam, fspec) && get((void**)&s->P, fspec) && get((void**)&s->seg0, fspec) &&
          get((void**)&s->part, sizeof(double) * 2 * xg) && get((void**)&s->d_acc, 2 * sizeof(double));
     g->bytes += s->bytes;
     if (!ok) {
@@ -278,8 +280,7 @@ static evx_status adj_alloc(evx_grid* g, int K, int nseg) {
 
 // one forward step S_in -> S_out, keeping c (real rows) and G = F_y F_z g
 static evx_status fwd_step_store(evx_grid* g, const float2* S_in, float* c_out, float2* G_out,
-                                 float2* S_out) {
-    cudaStream_t st = g->st;
+                                 float2* S_out, cudaStream_t st) {
     CKA(launch_spass(y_args(g, S_in, g->W), +1, st));
     ZPassArgs z = z_args(g);
     z.in = g->W;
@@ -360,36 +361,69 @@ extern "C" evx_status evx_ch_adjoint(evx_grid* g, const float* d_c0, int n_steps
     if (xsm > 48 * 1024)
         CKA(cudaFuncSetAttribute(xadj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm));
     const long long nspec = (long long)g->nx * g->ny * g->Zp;
-    for (int seg = nseg - 1; seg >= 0; --seg) {
-        const int n0 = seg * K;
-        const int n = std::min(K, n_steps - n0);
-        // recompute the segment's forward states
+    // one segment from S_start: recompute its n forward states, then its n adjoint steps
+    auto segment = [&](const float2* S_start, int n, cudaStream_t sst) -> evx_status {
         for (int j = 0; j < n; ++j) {
-            const float2* S_in = j == 0 ? A->ck[seg] : A->Sn[j - 1];
-            s = fwd_step_store(g, S_in, A->cs[j], A->G[j], A->Sn[j]);
-            if (s != EVX_OK) return s;
+            const float2* S_in = j == 0 ? S_start : A->Sn[j - 1];
+            evx_status r = fwd_step_store(g, S_in, A->cs[j], A->G[j], A->Sn[j], sst);
+            if (r != EVX_OK) return r;
         }
-        // adjoint steps n0 + n - 1 .. n0
         for (int j = n - 1; j >= 0; --j) {
-            xa.Lam = A->Lam;
-            xa.Sn1 = A->Sn[j];
-            xa.Gn = A->G[j];
-            xa.P = A->P;
-            xa.T = g->W;
-            xadj_kernel<<<dim3(xa.nchunks, xa.ny), NT, xsm, st>>>(xa);
+            XAdjArgs x = xa;
+            x.Lam = A->Lam;
+            x.Sn1 = A->Sn[j];
+            x.Gn = A->G[j];
+            x.P = A->P;
+            x.T = g->W;
+            xadj_kernel<<<dim3(x.nchunks, x.ny), NT, xsm, sst>>>(x);
             CKA(cudaGetLastError());
-            accum_partials_kernel<<<1, 1024, 0, st>>>(A->part, xg, A->d_acc + 0, 1.0 / V);
-            accum_partials_kernel<<<1, 1024, 0, st>>>(A->part + xg, xg, A->d_acc + 1, 1.0 / V);
+            accum_partials_kernel<<<1, 1024, 0, sst>>>(A->part, xg, A->d_acc + 0, 1.0 / V);
+            accum_partials_kernel<<<1, 1024, 0, sst>>>(A->part + xg, xg, A->d_acc + 1, 1.0 / V);
             CKA(cudaGetLastError());
-            CKA(launch_spass(y_args(g, g->W, g->W), +1, st));
+            CKA(launch_spass(y_args(g, g->W, g->W), +1, sst));
             ZPassArgs z = z_args(g);
             z.in = g->W;
             z.out = g->W;
             z.cn = A->cs[j];
             z.cnpitch = g->nz;
-            CKA(launch_zpass(z, Z_ADJ, st));
-            CKA(launch_spass(y_args(g, g->W, g->W), -1, st));
-            CKA(launch_cadd(A->P, g->W, A->Lam, nspec, st));
+            CKA(launch_zpass(z, Z_ADJ, sst));
+            CKA(launch_spass(y_args(g, g->W, g->W), -1, sst));
+            CKA(launch_cadd(A->P, g->W, A->Lam, nspec, sst));
+        }
+        return EVX_OK;
+    };
+    // full segments replay one captured graph (about 11 launches per step) whose
+    // input is the seg0 buffer; a shorter last segment runs eagerly
+    cudaGraphExec_t gexec = nullptr;
+    if (n_steps >= K && nseg > (n_steps % K ? 1 : 0)) {
+        cudaGraph_t graph = nullptr;
+        CKA(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+        evx_status r = segment(A->seg0, K, g->cap);
+        cudaError_t e2 = cudaStreamEndCapture(g->cap, &graph);
+        if (r != EVX_OK || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (r != EVX_OK) return r;
+            return set_error(g, EVX_ERR_CUDA, "adjoint segment capture failed");
+        }
+        cudaError_t e3 = cudaGraphInstantiate(&gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) return set_error(g, EVX_ERR_CUDA, "adjoint segment graph instantiation failed");
+    }
+    struct ExecGuard {
+        cudaGraphExec_t* e;
+        ~ExecGuard() {
+            if (*e) cudaGraphExecDestroy(*e);
+        }
+    } eg_{&gexec};
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int n0 = seg * K;
+        const int n = std::min(K, n_steps - n0);
+        if (n == K && gexec) {
+            CKA(cudaMemcpyAsync(A->seg0, A->ck[seg], fspec, cudaMemcpyDeviceToDevice, st));
+            CKA(cudaGraphLaunch(gexec, st));
+        } else {
+            s = segment(A->ck[seg], n, st);
+            if (s != EVX_OK) return s;
         }
     }
     // dL/dc_0 = lambda_0 in real space

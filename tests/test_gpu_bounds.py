@@ -23,7 +23,7 @@ import numpy as np, torch
 from paper_2507_21748_gb300 import evx, inputs
 en, line = evx.debug_bounds()
 assert en == 1, "not the bounds-checked build"
-shapes = [(8, 8, 8), (16, 32, 64), (48, 40, 36), (24, 30, 50), (10, 12, 14), (400, 16, 20), (64, 64, 128)]
+shapes = [(8, 8, 8), (16, 32, 64), (48, 40, 36), (24, 30, 50), (10, 12, 18), (400, 16, 20), (64, 64, 128)]
 for shape in shapes:
     c0 = torch.from_numpy(inputs.uniform_field(shape, seed=1, offset=0.1, lo=-0.4, hi=0.4)).cuda()
     for model in ("ch", "ac", "vm"):

@@ -36,26 +36,6 @@ using namespace evx;
 
 namespace evx {
 
-struct XAdjArgs {
-    const float2* Lam;   // Lambda_{n+1}
-    const float2* Sn1;   // S_{n+1}
-    const float2* Gn;    // G_n
-    float2* P;
-    float2* T;
-    int L;
-    long long rs, os;
-    int YB;
-    long long os2;
-    int ny, ncols, nchunks, M;
-    Plan plan;
-    const float2* tw;
-    const float* k2x;
-    const float* k2y;
-    const float* k2z;
-    float dt, dtM, dtMk, dtk, invL;
-    double* partials;    // [2 * nblocks]: kappa partials, then M partials
-};
-
 __device__ __forceinline__ double block_sum_d(double v, double* ws) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -375,8 +355,12 @@ extern "C" evx_status evx_ch_adjoint(evx_grid* g, const float* d_c0, int n_steps
             x.Gn = A->G[j];
             x.P = A->P;
             x.T = g->W;
-            xadj_kernel<<<dim3(x.nchunks, x.ny), NT, xsm, sst>>>(x);
-            CKA(cudaGetLastError());
+            cudaError_t fe = cudaSuccess;
+            if (!fast_xadj(x, sst, &fe)) {
+                xadj_kernel<<<dim3(x.nchunks, x.ny), NT, xsm, sst>>>(x);
+                fe = cudaGetLastError();
+            }
+            CKA(fe);
             accum_partials_kernel<<<1, 1024, 0, sst>>>(A->part, xg, A->d_acc + 0, 1.0 / V);
             accum_partials_kernel<<<1, 1024, 0, sst>>>(A->part + xg, xg, A->d_acc + 1, 1.0 / V);
             CKA(cudaGetLastError());

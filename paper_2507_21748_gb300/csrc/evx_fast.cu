@@ -664,6 +664,123 @@ __global__ void __launch_bounds__(8 * TP, SEP ? 1 : (8 * TP >= 128 ? 3 : 1))
     if (threadIdx.x == 0) bulk_wait0();
 }
 
+// ------------------------------------------------------ adjoint x pass
+// One tile = 8 columns (kz) of one ky line, all nx rows; 8 TP threads, thread
+// (p, n2) owns column p and rows n2 + TP n1 (loads and stores go straight
+// between global memory and registers; 64-byte row segments per 8 threads).
+// lambda_hat = F_x Lambda stays in registers while F_x S_{n+1} and F_x G_n pass
+// through for the parameter-gradient partials; then P = F_x^-1(a lambda_hat)/nx
+// and T = F_x^-1(b lambda_hat)/nx, a = 1/D, b = -dt M |k|^2 / D, D = 1 + dt M kappa |k|^4.
+// Partials (FP32 per thread, FP64 per CTA):
+//   kappa: w Re(conj(lambda_hat) c_hat) (-dt M |k|^4 / D)
+//   M:     w Re(conj(lambda_hat) c_hat) (-dt kappa |k|^4 / D) + w Re(conj(lambda_hat) g_hat) (-dt |k|^2 / D)
+// with w = 1 for kz = 0 or M and 2 otherwise (Hermitian half spectrum).
+template <int R1, int TP>
+__global__ void __launch_bounds__(8 * TP) fxadj_kernel(XAdjArgs a) {
+    constexpr int P = 8, L = R1 * TP, NB = R1 / TP, NT = P * TP;
+    extern __shared__ __align__(16) float4 smem4[];
+    float2* xb = reinterpret_cast<float2*>(smem4);  // [(L + TP) P] transposes
+    float2* tA = xb + (L + TP) * P;
+    float2* tB = NB == 1 ? tA : tA + L;
+    fill_twiddles<R1, TP>(tA, tB, a.tw, NT);
+    __shared__ double red[2][NT / 32 + 1];
+    const int p = threadIdx.x % P, n2 = threadIdx.x / P;
+    const int chunk = blockIdx.x, ky = blockIdx.y;
+    const int kz = chunk * P + p;
+    const bool valid = kz < a.ncols;
+    const long long base = split_off(ky, a.YB, a.os, a.os2) + (long long)chunk * P + p;
+    const float k2yz = a.k2y[ky] + (valid ? a.k2z[kz] : 0.f);
+    const float w = (kz == 0 || kz == a.M) ? 1.f : 2.f;
+    __syncthreads();
+    auto forward = [&](const float2* f, float2 (&v)[R1]) {
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1)
+            v[n1] = valid ? f[base + (long long)(n2 + TP * n1) * a.rs] : make_float2(0.f, 0.f);
+        Dft<R1, -1>::run(v);
+        twiddle_a<R1, TP, -1>(v, n2, tA);
+        __syncthreads();  // earlier reads of xb done
+        t1_s<R1, TP, P>(v, xb, n2, p);
+        pass_b<R1, TP, -1>(v);
+    };
+    auto inverse_store = [&](float2 (&v)[R1], float2* out) {
+        pass_b<R1, TP, 1>(v);
+        twiddle_b<R1, TP, 1>(v, n2, tB);
+        __syncthreads();
+        t2_s<R1, TP, P>(v, xb, n2, p);
+        Dft<R1, 1>::run(v);
+        if (valid)
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) out[base + (long long)(n2 + TP * n1) * a.rs] = v[n1];
+    };
+    float2 lam[R1], v[R1];
+    forward(a.Lam, lam);
+    float acck = 0.f, accm = 0.f;
+    forward(a.Sn1, v);
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+        for (int c = 0; c < TP; ++c) {
+            const float k2 = a.k2x[n2 * NB + i + R1 * c] + k2yz, k4 = k2 * k2;
+            const float Dinv = rcp_approx(fmaf(a.dtMk, k4, 1.f));
+            const float2 l = lam[i * TP + c], ch = v[i * TP + c];
+            const float re = valid ? w * fmaf(l.x, ch.x, l.y * ch.y) : 0.f;
+            acck = fmaf(re, -a.dtM * k4 * Dinv, acck);
+            accm = fmaf(re, -a.dtk * k4 * Dinv, accm);
+        }
+    forward(a.Gn, v);
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+        for (int c = 0; c < TP; ++c) {
+            const float k2 = a.k2x[n2 * NB + i + R1 * c] + k2yz;
+            const float Dinv = rcp_approx(fmaf(a.dtMk, k2 * k2, 1.f));
+            const float2 l = lam[i * TP + c], gh = v[i * TP + c];
+            const float re = valid ? w * fmaf(l.x, gh.x, l.y * gh.y) : 0.f;
+            accm = fmaf(re, -a.dt * k2 * Dinv, accm);
+        }
+    // P = F_x^-1 (a lambda_hat) / nx
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+        for (int c = 0; c < TP; ++c) {
+            const float k2 = a.k2x[n2 * NB + i + R1 * c] + k2yz;
+            v[i * TP + c] = cscale(lam[i * TP + c], a.invL * rcp_approx(fmaf(a.dtMk, k2 * k2, 1.f)));
+        }
+    inverse_store(v, a.P);
+    // T = F_x^-1 (b lambda_hat) / nx
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+        for (int c = 0; c < TP; ++c) {
+            const float k2 = a.k2x[n2 * NB + i + R1 * c] + k2yz;
+            v[i * TP + c] = cscale(lam[i * TP + c], -a.dtM * k2 * a.invL * rcp_approx(fmaf(a.dtMk, k2 * k2, 1.f)));
+        }
+    inverse_store(v, a.T);
+    // per-CTA FP64 partials, fixed order
+    double dk = acck, dm = accm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dk += __shfl_down_sync(0xffffffffu, dk, o);
+        dm += __shfl_down_sync(0xffffffffu, dm, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = dk;
+        red[1][threadIdx.x >> 5] = dm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sk = 0.0, sm = 0.0;
+        for (int q = 0; q < (NT + 31) / 32; ++q) {
+            sk += red[0][q];
+            sm += red[1][q];
+        }
+        const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+        const long long nblk = (long long)gridDim.x * gridDim.y;
+        a.partials[blk] = sk;
+        a.partials[nblk + blk] = sm;
+    }
+}
+
 }  // namespace fast
 
 // --------------------------------------------------------------- dispatch
@@ -895,6 +1012,30 @@ bool fast_zconv(const ZPassArgs& a, int dir, cudaStream_t st, cudaError_t* err, 
         case 256: *err = run_fzconv<32, 8>(a, dir, st, grid_used); return true;
         case 512: *err = run_fzconv<32, 16>(a, dir, st, grid_used); return true;
         case 200: *err = run_fzconv<20, 10>(a, dir, st, grid_used); return true;
+    }
+    return false;
+}
+
+template <int R1, int TP>
+static cudaError_t run_fxadj(const XAdjArgs& a, cudaStream_t st) {
+    constexpr int L = R1 * TP;
+    const size_t smem = sizeof(float2) * ((size_t)(L + TP) * 8 + (R1 == TP ? 1 : 2) * (size_t)L);
+    int per = 0;
+    cudaError_t e = prep(fast::fxadj_kernel<R1, TP>, smem, 8 * TP, &per);
+    if (e != cudaSuccess) return e;
+    fast::fxadj_kernel<R1, TP><<<dim3(a.nchunks, a.ny), 8 * TP, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+bool fast_xadj(const XAdjArgs& a, cudaStream_t st, cudaError_t* err) {
+    if (!fast_paths_enabled() || a.os * a.YB != a.rs) return false;
+    switch (a.L) {
+        case 64: *err = run_fxadj<32, 2>(a, st); return true;
+        case 128: *err = run_fxadj<32, 4>(a, st); return true;
+        case 256: *err = run_fxadj<32, 8>(a, st); return true;
+        case 512: *err = run_fxadj<32, 16>(a, st); return true;
+        case 1024: *err = run_fxadj<32, 32>(a, st); return true;
+        case 400: *err = run_fxadj<20, 20>(a, st); return true;
     }
     return false;
 }

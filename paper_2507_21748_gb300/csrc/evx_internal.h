@@ -90,6 +90,29 @@ struct XUpdArgs {
     const double* cbar; // model 3: FP64 mean (for g'(cbar))
 };
 
+// Adjoint x pass (evx_adjoint.cu, fast variant in evx_fast.cu): from
+// Lambda_{n+1}, S_{n+1} and G_n, P = F_x^-1(a lambda_hat)/nx, T = F_x^-1(b lambda_hat)/nx
+// and per-CTA FP64 partials of the two parameter gradients.
+struct XAdjArgs {
+    const float2* Lam;   // Lambda_{n+1}
+    const float2* Sn1;   // S_{n+1}
+    const float2* Gn;    // G_n
+    float2* P;
+    float2* T;
+    int L;
+    long long rs, os;
+    int YB;
+    long long os2;
+    int ny, ncols, nchunks, M;
+    Plan plan;
+    const float2* tw;
+    const float* k2x;
+    const float* k2y;
+    const float* k2z;
+    float dt, dtM, dtMk, dtk, invL;
+    double* partials;    // [2 * nblocks]: kappa partials, then M partials
+};
+
 // Energy: gradient term sum_k w(kz) |k|^2 |c_hat|^2 from the state S.
 struct XEnergyArgs {
     const float2* S;
@@ -200,6 +223,8 @@ constexpr int SUM_BLOCKS = 1216;  // 8 x 152 SMs
 bool fast_spass(const SPassArgs& a, int dir, cudaStream_t st, cudaError_t* err);
 bool fast_xupdate(const XUpdArgs& a, cudaStream_t st, cudaError_t* err);
 bool fast_zstep(const ZPassArgs& a, cudaStream_t st, cudaError_t* err, int* grid_used, bool adj = false);
+// adjoint x pass with the four-step transforms; false if the length has no fast kernel
+bool fast_xadj(const XAdjArgs& a, cudaStream_t st, cudaError_t* err);
 bool fast_zconv(const ZPassArgs& a, int dir, cudaStream_t st, cudaError_t* err, int* grid_used);
 bool fast_paths_enabled();  // false when the environment sets EVX_GENERIC=1
 // reads (and optionally clears) the flag a bounded TMA wait sets when it gives up

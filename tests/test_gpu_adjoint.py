@@ -51,7 +51,8 @@ def gpu_adjoint(evx, c0, n, ckpt, M, kappa, dLdcN):
 
 
 @pytest.mark.parametrize("shape,n,ckpt", [((24, 20, 16), 7, 3), ((32, 32, 32), 12, 5),
-                                          ((64, 64, 64), 40, 20)])
+                                          ((64, 64, 64), 40, 20), ((128, 64, 256), 10, 4),
+                                          ((400, 16, 24), 6, 3), ((1024, 8, 16), 5, 5)])
 def test_adjoint_vs_oracle(evx, shape, n, ckpt):
     c0 = inputs.uniform_field(shape, seed=21, lo=-0.3, hi=0.3, offset=0.1)
     target = O.ch_step(c0, DT, 0.8, 1.5, H, n, check_imag=False)

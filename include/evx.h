@@ -110,7 +110,11 @@ evx_status evx_set_field_host(evx_grid *g, const float *h_c);
  * caller's device buffer d_out (nx*ny*nz float32). Asynchronous. */
 evx_status evx_get_field(evx_grid *g, float *d_out);
 
-/* Same into host memory; synchronises the stream. */
+/* Same into host memory; synchronises the stream. When h_out is page-locked
+ * host memory mapped into the device's address space (cudaHostAlloc or
+ * cudaMallocHost under unified addressing), the inverse transform writes the
+ * field straight into it; other host memory is filled through a device
+ * staging buffer and copies. */
 evx_status evx_get_field_host(evx_grid *g, float *h_out);
 
 /* Advance the state by n_steps >= 0 semi-implicit Cahn-Hilliard steps

@@ -589,6 +589,18 @@ evx_status evx_get_field_host(evx_grid* g, float* h_out) {
         CK(cudaStreamSynchronize(g->st));
         return check_timeouts(g);
     }
+    // pinned host memory that the device can address (page-locked and mapped, as
+    // cudaHostAlloc / torch pin_memory give under unified addressing): the C2R
+    // writes the caller-order rows straight into it, with no staging copy
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h_out) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
+        ((uintptr_t)at.devicePointer & 15) == 0) {
+        evx_status s = store_real(g, (float*)at.devicePointer, g->nz, nullptr, 1);
+        if (s != EVX_OK) return s;
+        CK(cudaStreamSynchronize(g->st));
+        return check_timeouts(g);
+    }
+    cudaGetLastError();  // pageable memory: the attribute query may leave an error behind
     evx_status s = store_real(g, (float*)g->W, 2LL * g->Zp, nullptr, 0);
     if (s != EVX_OK) return s;
     s = host_rows_copy(g, h_out, false);

@@ -196,10 +196,13 @@ def test_host_io_matches_device_io(evx, shape):
     g2.set_field(torch.from_numpy(c0).cuda())
     g2.step(3)
     c = g2.get_field().cpu()
+    pageable = torch.empty(shape, dtype=torch.float32)  # not pinned: the staged copy path
+    g.get_field_host(pageable)
     g.close()
     g2.close()
     assert torch.equal(a, b)
     assert torch.equal(a, c)
+    assert torch.equal(pageable, b)
 
 
 def test_nonfinite_detected(evx):

@@ -688,6 +688,10 @@ def main():
     if not args.no_e2e:
         host_in = torch.from_numpy(c0).pin_memory()
         host_out = torch.empty(shape, dtype=torch.float32).pin_memory()
+        # one untimed pass through the same buffers: the first transfers from and to
+        # freshly pinned pages carry a one-time mapping cost (measured 60-200 ms here)
+        g.set_field_host(host_in)
+        g.get_field_host(host_out)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -699,8 +703,10 @@ def main():
         te = max_over_ranks(t1 - t0)
         e2e = {"value": job_throughput(ws, args.steps, V, te), "unit": UNIT,
                "h2d_bytes_per_step": 4.0 * V / args.steps, "d2h_bytes_per_step": 4.0 * V / args.steps,
-               "job": "pinned host c0 -> evx_set_field_host -> %d steps -> evx_get_field_host; "
-                      "the field's bytes are spread over the job's steps" % args.steps}
+               "job": "pinned host c0 -> evx_set_field_host -> %d steps -> evx_get_field_host (the result is "
+                      "written by the inverse transform straight into the mapped pinned buffer); the field's "
+                      "bytes are spread over the job's steps; one untimed pass through the same buffers first"
+                      % args.steps}
         del host_in, host_out
     fp = g.footprint()  # the Cahn-Hilliard workload's footprint (the VM model adds a buffer)
     # ---- the Allen-Cahn model on the same engine and grid (device-resident)

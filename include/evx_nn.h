@@ -39,7 +39,9 @@ enum {
     EVX_NN_EPI_GELU = 1,     /* pre (BF16) = value; out (BF16) = GELU(value) (erf form) */
     EVX_NN_EPI_RESID = 2,    /* out (BF16) = res + value */
     EVX_NN_EPI_GELU_BWD = 3, /* out (BF16) = value * GELU'(pre) (pre read, not written) */
-    EVX_NN_EPI_FIELD = 4     /* out (FP32 field) = value of channel 0 */
+    EVX_NN_EPI_FIELD = 4,    /* out (FP32 field) = value of channel 0 */
+    EVX_NN_EPI_RESID32 = 5   /* FP32 residual stream: pre (FP32 [..][cout]) += value, updated in
+                              * place; out (BF16) = the new pre (the next convolution's input) */
 };
 
 /* Periodic 3x3x3 convolution in (BF16, cin channels) -> out, weights w
@@ -65,6 +67,14 @@ evx_status evx_nn_lift(const float *f, float scale, const void *w, int cin, int 
                        int B, int X, int Y, int Z, void *stream);
 evx_status evx_nn_project(const void *h, const void *w, int cin, int cout, const float *bias, float *out, int B,
                           int X, int Y, int Z, void *stream);
+/* The same two with an FP32 residual stream (EVX_NN_EPI_RESID32): evx_nn_lift32
+ * writes the lift both as FP32 out32 [..][32] and as its BF16 copy out;
+ * evx_nn_project32 reads the FP32 stream h32 [..][32]. The stream keeps FP32
+ * precision between the blocks; only the convolutions' operands are BF16. */
+evx_status evx_nn_lift32(const float *f, float scale, const void *w, int cin, int cout, const float *bias,
+                         void *out, float *out32, int B, int X, int Y, int Z, void *stream);
+evx_status evx_nn_project32(const float *h32, const void *w, int cin, int cout, const float *bias, float *out,
+                            int B, int X, int Y, int Z, void *stream);
 
 /* Weight gradient of out = conv(x, W): dw[t][co][ci] = sum_v dy(v, co) x(v + off_t, ci)
  * (FP32). partials: device scratch of partial_floats floats (at least

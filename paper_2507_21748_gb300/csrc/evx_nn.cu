@@ -133,6 +133,12 @@ __global__ void __launch_bounds__(NTHR) conv_fwd_kernel(ConvArgs a) {
                     const float2 q = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(a.res + o));
                     v0 += q.x;
                     v1 += q.y;
+                } else if (EPI == EVX_NN_EPI_RESID32) {  // FP32 stream in a.pre, updated in place
+                    float2* sp = reinterpret_cast<float2*>(reinterpret_cast<float*>(a.pre) + o);
+                    const float2 q = *sp;
+                    v0 += q.x;
+                    v1 += q.y;
+                    *sp = make_float2(v0, v1);
                 }
                 *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(a.out) + o) =
                     __floats2bfloat162_rn(v0, v1);
@@ -425,10 +431,12 @@ __device__ __forceinline__ void vox_coords(long long v, int X, int Y, int Z, int
 }
 
 // out(v, co) = bias(co) + sum_t w[t][co][0] BF16(scale f(v + off_t)), co < 32
+// F32: the FP32-stream variant (the field enters unrounded; out32 receives the FP32 sums)
+template <bool F32>
 __global__ void __launch_bounds__(256) lift_direct_kernel(const float* __restrict__ f, float scale,
                                                            const __nv_bfloat16* __restrict__ w, int wcin,
-                                                           const float* __restrict__ bias, __nv_bfloat16* out, int B,
-                                                           int X, int Y, int Z) {
+                                                           const float* __restrict__ bias, __nv_bfloat16* out,
+                                                           float* __restrict__ out32, int B, int X, int Y, int Z) {
     __shared__ float4 ws[27][8];  // w[t][co][0], co = 4 q .. 4 q + 3
     __shared__ float bs[32];
     for (int i = threadIdx.x; i < 27 * 32; i += blockDim.x) {
@@ -451,8 +459,8 @@ __global__ void __launch_bounds__(256) lift_direct_kernel(const float* __restric
             const int xx = x + dx < 0 ? X - 1 : (x + dx == X ? 0 : x + dx);
             const int yy = y + dy < 0 ? Y - 1 : (y + dy == Y ? 0 : y + dy);
             const int zz = z + dz < 0 ? Z - 1 : (z + dz == Z ? 0 : z + dz);
-            const float val =
-                __bfloat162float(__float2bfloat16_rn(scale * f[(((long long)b * X + xx) * Y + yy) * Z + zz]));
+            const float fv = scale * f[(((long long)b * X + xx) * Y + yy) * Z + zz];
+            const float val = F32 ? fv : __bfloat162float(__float2bfloat16_rn(fv));
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const float4 wq = ws[t][q];
@@ -471,12 +479,20 @@ __global__ void __launch_bounds__(256) lift_direct_kernel(const float* __restric
             for (int j = 0; j < 4; ++j) pp[j] = __floats2bfloat162_rn(acc[8 * q + 2 * j], acc[8 * q + 2 * j + 1]);
             o[q] = pk;
         }
+        if (F32) {
+            float4* o32 = reinterpret_cast<float4*>(out32 + v * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o32[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
     }
 }
 
 // out(v) = bias(0) + sum_t sum_ci w[t][0][ci] h(v + off_t, ci), ci < 32, FP32 field;
 // w is [27][wcout][32] (row 0 of each tap used)
+// F32: reads the FP32 residual stream h32 instead of the BF16 activations h
+template <bool F32>
 __global__ void __launch_bounds__(256) project_direct_kernel(const __nv_bfloat16* __restrict__ h,
+                                                              const float* __restrict__ h32,
                                                               const __nv_bfloat16* __restrict__ w, int wcout,
                                                               const float* __restrict__ bias, float* out, int B,
                                                               int X, int Y, int Z) {
@@ -499,7 +515,20 @@ __global__ void __launch_bounds__(256) project_direct_kernel(const __nv_bfloat16
             const int xx = x + dx < 0 ? X - 1 : (x + dx == X ? 0 : x + dx);
             const int yy = y + dy < 0 ? Y - 1 : (y + dy == Y ? 0 : y + dy);
             const int zz = z + dz < 0 ? Z - 1 : (z + dz == Z ? 0 : z + dz);
-            const uint4* hp = reinterpret_cast<const uint4*>(h + ((((long long)b * X + xx) * Y + yy) * Z + zz) * 32);
+            const long long vi = (((long long)b * X + xx) * Y + yy) * Z + zz;
+            if (F32) {
+                const float4* hp = reinterpret_cast<const float4*>(h32 + vi * 32);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 hv = hp[q], wq = ws[t][q];
+                    acc = fmaf(wq.x, hv.x, acc);
+                    acc = fmaf(wq.y, hv.y, acc);
+                    acc = fmaf(wq.z, hv.z, acc);
+                    acc = fmaf(wq.w, hv.w, acc);
+                }
+                continue;
+            }
+            const uint4* hp = reinterpret_cast<const uint4*>(h + vi * 32);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint4 hv = hp[q];
@@ -576,6 +605,7 @@ evx_status conv_epi(int epi, const ConvArgs& a, cudaStream_t st) {
         case EVX_NN_EPI_PLAIN: return launch_conv<CIN, COUT, EVX_NN_EPI_PLAIN>(a, st);
         case EVX_NN_EPI_GELU: return launch_conv<CIN, COUT, EVX_NN_EPI_GELU>(a, st);
         case EVX_NN_EPI_RESID: return launch_conv<CIN, COUT, EVX_NN_EPI_RESID>(a, st);
+        case EVX_NN_EPI_RESID32: return launch_conv<CIN, COUT, EVX_NN_EPI_RESID32>(a, st);
         case EVX_NN_EPI_GELU_BWD: return launch_conv<CIN, COUT, EVX_NN_EPI_GELU_BWD>(a, st);
         case EVX_NN_EPI_FIELD: return launch_conv<CIN, COUT, EVX_NN_EPI_FIELD>(a, st);
     }
@@ -634,6 +664,8 @@ evx_status evx_nn_conv3d(const void* in, const void* w, const float* bias, void*
     if ((epilogue == EVX_NN_EPI_GELU || epilogue == EVX_NN_EPI_GELU_BWD) && !pre)
         return nn_fail(EVX_ERR_ARG, "GELU epilogues need the pre-activation buffer");
     if (epilogue == EVX_NN_EPI_RESID && !res) return nn_fail(EVX_ERR_ARG, "residual epilogue needs res");
+    if (epilogue == EVX_NN_EPI_RESID32 && (!pre || cout != 32))
+        return nn_fail(EVX_ERR_ARG, "the FP32-stream epilogue needs the stream in pre and cout = 32");
     ConvArgs a{};
     a.in = (const __nv_bfloat16*)in;
     a.w = (const __nv_bfloat16*)w;
@@ -658,8 +690,18 @@ evx_status evx_nn_lift(const float* f, float scale, const void* w, int cin, int 
     if (!f || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
     if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
     if (cout != 32 || cin < 1) return nn_fail(EVX_ERR_ARG, "lift: cout must be 32, cin >= 1");
-    lift_direct_kernel<<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
-        f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, B, X, Y, Z);
+    lift_direct_kernel<false><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+        f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, nullptr, B, X, Y, Z);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_lift32(const float* f, float scale, const void* w, int cin, int cout, const float* bias, void* out,
+                         float* out32, int B, int X, int Y, int Z, void* stream) {
+    if (!f || !w || !out || !out32) return nn_fail(EVX_ERR_ARG, "NULL pointer");
+    if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
+    if (cout != 32 || cin < 1) return nn_fail(EVX_ERR_ARG, "lift: cout must be 32, cin >= 1");
+    lift_direct_kernel<true><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+        f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, out32, B, X, Y, Z);
     return nn_cuda(cudaGetLastError());
 }
 
@@ -668,8 +710,18 @@ evx_status evx_nn_project(const void* h, const void* w, int cin, int cout, const
     if (!h || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
     if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
     if (cin != 32 || cout < 1) return nn_fail(EVX_ERR_ARG, "project: cin must be 32, cout >= 1");
-    project_direct_kernel<<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16*)h, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
+    project_direct_kernel<false><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)h, nullptr, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
+    return nn_cuda(cudaGetLastError());
+}
+
+evx_status evx_nn_project32(const float* h32, const void* w, int cin, int cout, const float* bias, float* out, int B,
+                            int X, int Y, int Z, void* stream) {
+    if (!h32 || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
+    if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
+    if (cin != 32 || cout < 1) return nn_fail(EVX_ERR_ARG, "project: cin must be 32, cout >= 1");
+    project_direct_kernel<true><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+        nullptr, h32, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
     return nn_cuda(cudaGetLastError());
 }
 

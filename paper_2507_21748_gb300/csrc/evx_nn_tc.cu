@@ -197,6 +197,17 @@ __device__ __forceinline__ void epilogue_store(const ConvArgs& a, long long vox,
                 const float2 rf = __bfloat1622float2(rp[j]);
                 ow[j] = __floats2bfloat162_rn(v[2 * j] + rf.x, v[2 * j + 1] + rf.y);
             }
+        } else if (EPI == EVX_NN_EPI_RESID32) {  // FP32 stream in a.pre, updated in place
+            float4* sp = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.pre) + o + q * 8);
+            float4 s0 = sp[0], s1 = sp[1];
+            s0.x += v[0], s0.y += v[1], s0.z += v[2], s0.w += v[3];
+            s1.x += v[4], s1.y += v[5], s1.z += v[6], s1.w += v[7];
+            sp[0] = s0;
+            sp[1] = s1;
+            ow[0] = __floats2bfloat162_rn(s0.x, s0.y);
+            ow[1] = __floats2bfloat162_rn(s0.z, s0.w);
+            ow[2] = __floats2bfloat162_rn(s1.x, s1.y);
+            ow[3] = __floats2bfloat162_rn(s1.z, s1.w);
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) ow[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
@@ -722,6 +733,7 @@ cudaError_t conv32_tc(const ConvArgs& a, int epilogue, cudaStream_t st, int sms)
         case EVX_NN_EPI_GELU: return conv32_tc_epi<EVX_NN_EPI_GELU>(a, st, sms);
         case EVX_NN_EPI_RESID: return conv32_tc_epi<EVX_NN_EPI_RESID>(a, st, sms);
         case EVX_NN_EPI_GELU_BWD: return conv32_tc_epi<EVX_NN_EPI_GELU_BWD>(a, st, sms);
+        case EVX_NN_EPI_RESID32: return conv32_tc_epi<EVX_NN_EPI_RESID32>(a, st, sms);
     }
     return cudaErrorInvalidValue;
 }

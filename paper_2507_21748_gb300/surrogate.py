@@ -19,8 +19,8 @@ NN_EXPORTS = ["evx_nn_conv3d", "evx_nn_conv3d_wgrad", "evx_nn_bias_grad", "evx_n
               "evx_nn_field_to_act", "evx_nn_zero_mean_add", "evx_nn_mse", "evx_nn_adam",
               "evx_nn_f32_to_bf16", "evx_nn_set_conv_engine", "evx_nn_conv_engine", "evx_nn_check",
               "evx_nn_lift", "evx_nn_project", "evx_nn_abs_sum", "evx_nn_zero_mean_add_scaled",
-              "evx_nn_nl_scale", "evx_nn_last_error"]
-EPI_PLAIN, EPI_GELU, EPI_RESID, EPI_GELU_BWD, EPI_FIELD = range(5)
+              "evx_nn_nl_scale", "evx_nn_lift32", "evx_nn_project32", "evx_nn_last_error"]
+EPI_PLAIN, EPI_GELU, EPI_RESID, EPI_GELU_BWD, EPI_FIELD, EPI_RESID32 = range(6)
 ENGINE_TCGEN05, ENGINE_MMA_SYNC = 0, 1
 
 
@@ -42,6 +42,8 @@ def _setup():
         "evx_nn_set_conv_engine": [i],
         "evx_nn_lift": [vp, f, vp, i, i, vp, vp, i, i, i, i, vp],
         "evx_nn_project": [vp, vp, i, i, vp, vp, i, i, i, i, vp],
+        "evx_nn_lift32": [vp, f, vp, i, i, vp, vp, vp, i, i, i, i, vp],
+        "evx_nn_project32": [vp, vp, i, i, vp, vp, i, i, i, i, vp],
         "evx_nn_conv_engine": [],
         "evx_nn_check": [],
     }
@@ -93,9 +95,13 @@ class Net:
     CIN = 16  # the input field is padded to 16 channels (channel 0 = c)
     CPROJ = 16  # the projection writes 16 channels, channel 0 is used
 
-    def __init__(self, shape, batch, width=32, nblocks=4, seed=0, train=True, proj_gain=0.01):
+    def __init__(self, shape, batch, width=32, nblocks=4, seed=0, train=True, proj_gain=0.01, f32_stream=True):
         assert width == 32
         self.shape, self.batch, self.W, self.nb = tuple(shape), int(batch), width, nblocks
+        # f32_stream: the residual stream h is kept in FP32 (the field enters the lift
+        # unrounded, each block adds its output to the FP32 stream, the projection reads
+        # it); the convolutions still take BF16 operands (a BF16 copy of the stream)
+        self.f32 = bool(f32_stream)
         self.training = train
         self.V = int(np.prod(self.shape))
         self.nvox = self.V * self.batch
@@ -137,6 +143,7 @@ class Net:
             # inference: the residual stream is updated in place; one GELU input/output pair
             h, u, a = (torch.empty((nv, W), dtype=bf, device=dev) for _ in range(3))
             self.h, self.u, self.a = [h] * (nblocks + 1), [u] * nblocks, [a] * nblocks
+            self.h32 = torch.empty((nv, W), dtype=torch.float32, device=dev) if self.f32 else None
             self.d = torch.empty(nv, dtype=torch.float32, device=dev)
             self.pred = torch.empty(nv, dtype=torch.float32, device=dev)
             sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -145,6 +152,7 @@ class Net:
             self.spart = torch.empty(3 * self.nparts * self.batch, dtype=torch.float64, device=dev)
             return
         self.h = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks + 1)]
+        self.h32 = torch.empty((nv, W), dtype=torch.float32, device=dev) if self.f32 else None
         self.u = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks)]
         self.a = [torch.empty((nv, W), dtype=bf, device=dev) for _ in range(nblocks)]
         self.d = torch.empty(nv, dtype=torch.float32, device=dev)
@@ -219,7 +227,10 @@ class Net:
         X, Y, Z = self.shape
         if self.training:  # the padded input is kept for the lift's weight gradient
             _ck(lib.evx_nn_field_to_act(_p(c), self.nvox, self.CIN, 1.0, _p(self.a_in), s))
-        if W == 32:  # direct sum: only input channel 0 is nonzero
+        if W == 32 and self.f32:  # direct sum, FP32 stream and its BF16 copy
+            _ck(lib.evx_nn_lift32(_p(c), 1.0, _p(self.wbf["W0"]), self.CIN, W, _p(self.p["b0"]), _p(self.h[0]),
+                                  _p(self.h32), self.batch, X, Y, Z, s))
+        elif W == 32:  # direct sum: only input channel 0 is nonzero
             _ck(lib.evx_nn_lift(_p(c), 1.0, _p(self.wbf["W0"]), self.CIN, W, _p(self.p["b0"]), _p(self.h[0]),
                                 self.batch, X, Y, Z, s))
         else:
@@ -228,9 +239,16 @@ class Net:
             self._conv(self.a_in, "W0", self.p["b0"], self.h[0], self.CIN, W, EPI_PLAIN)
         for k in range(self.nb):
             self._conv(self.h[k], "W1_%d" % k, self.p["b1_%d" % k], self.a[k], W, W, EPI_GELU, pre=self.u[k])
-            self._conv(self.a[k], "W2_%d" % k, self.p["b2_%d" % k], self.h[k + 1], W, W, EPI_RESID,
-                       res=self.h[k])
-        if W == 32:  # direct sum: only output channel 0 is used
+            if self.f32:  # h32 += conv2(a); BF16 copy of the new stream into h[k + 1]
+                self._conv(self.a[k], "W2_%d" % k, self.p["b2_%d" % k], self.h[k + 1], W, W, EPI_RESID32,
+                           pre=self.h32)
+            else:
+                self._conv(self.a[k], "W2_%d" % k, self.p["b2_%d" % k], self.h[k + 1], W, W, EPI_RESID,
+                           res=self.h[k])
+        if W == 32 and self.f32:
+            _ck(lib.evx_nn_project32(_p(self.h32), _p(self.wbf["Wp"]), W, self.CPROJ, _p(self.p["bp"]),
+                                     _p(self.d), self.batch, X, Y, Z, s))
+        elif W == 32:  # direct sum: only output channel 0 is used
             _ck(lib.evx_nn_project(_p(self.h[self.nb]), _p(self.wbf["Wp"]), W, self.CPROJ, _p(self.p["bp"]),
                                    _p(self.d), self.batch, X, Y, Z, s))
         else:

@@ -350,3 +350,64 @@ def test_nonlinearity_scale_and_scaled_zero_mean_add(S):
     dn = dd.cpu().numpy().astype(np.float64)
     ref = base.cpu().numpy() + np.array(want)[:, None] * (dn - dn.mean(axis=1, keepdims=True))
     assert np.abs(out.cpu().numpy() - ref).max() < 1e-5
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("shape", [(2, 4, 6, 64), (1, 3, 16, 128)])
+def test_conv_fp32_stream_epilogue(S, engine, shape):
+    """EVX_NN_EPI_RESID32: the FP32 stream in `pre` is updated in place (stream +=
+    conv + bias, within FP32 accumulation of the FP64 oracle's conv) and `out`
+    receives its BF16 copy; both engines."""
+    import torch
+    rng = np.random.default_rng(31 + engine + shape[2])
+    x = bf16(rng.standard_normal(shape + (32,)))
+    w = bf16(rng.standard_normal((27, 32, 32)) * 0.1)
+    b = torch.from_numpy(rng.standard_normal(32).astype(np.float32))
+    stream0 = rng.standard_normal(shape + (32,)).astype(np.float32)
+    xd, wd, bd = x.cuda(), w.cuda(), b.cuda()
+    h32 = torch.from_numpy(stream0).cuda()
+    out = torch.empty(shape + (32,), dtype=torch.bfloat16, device="cuda")
+    B, X, Y, Z = shape
+    S.set_conv_engine(engine)
+    try:
+        S._ck(S.lib.evx_nn_conv3d(S._p(xd), S._p(wd), S._p(bd), S._p(out), S._p(h32), None,
+                                  B, X, Y, Z, 32, 32, S.EPI_RESID32, S._stream()))
+        S.check()
+    finally:
+        S.set_conv_engine(S.ENGINE_TCGEN05)
+    ref = stream0.astype(np.float64) + N.conv(x.float().numpy().astype(np.float64),
+                                              w.float().numpy().astype(np.float64), b.numpy().astype(np.float64))
+    got32 = h32.cpu().numpy()
+    assert rel(got32, ref) < 5e-6  # FP32 accumulation, no BF16 rounding of the stream
+    assert rel(out.float().cpu().numpy(), ref) < 8e-3
+    assert torch.equal(out.cpu(), torch.from_numpy(got32).to(torch.bfloat16))
+
+
+def test_fp32_stream_lift_and_projection(S):
+    """evx_nn_lift32 (unrounded field, FP32 sums and their BF16 copy) and
+    evx_nn_project32 (reads the FP32 stream) against the FP64 oracle's conv."""
+    import torch
+    rng = np.random.default_rng(12)
+    shape = (2, 4, 6, 64)
+    B, X, Y, Z = shape
+    f = rng.uniform(-0.5, 0.5, shape).astype(np.float32)
+    w0 = bf16(rng.standard_normal((27, 32, 16)) * 0.2)
+    b0 = torch.from_numpy(rng.standard_normal(32).astype(np.float32))
+    out = torch.empty(shape + (32,), dtype=torch.bfloat16, device="cuda")
+    out32 = torch.empty(shape + (32,), dtype=torch.float32, device="cuda")
+    fd, w0d, b0d = torch.from_numpy(f).cuda(), w0.cuda(), b0.cuda()
+    S._ck(S.lib.evx_nn_lift32(S._p(fd), 1.0, S._p(w0d), 16, 32, S._p(b0d), S._p(out), S._p(out32),
+                              B, X, Y, Z, S._stream()))
+    xin = np.zeros(shape + (16,))
+    xin[..., 0] = f
+    ref = N.conv(xin, w0.float().numpy().astype(np.float64), b0.numpy().astype(np.float64))
+    assert rel(out32.cpu().numpy(), ref) < 2e-6
+    assert rel(out.float().cpu().numpy(), ref) < 8e-3
+    h32 = rng.standard_normal(shape + (32,)).astype(np.float32)
+    wp = bf16(rng.standard_normal((27, 16, 32)) * 0.1)
+    bp = torch.from_numpy(rng.standard_normal(16).astype(np.float32))
+    d = torch.empty(shape, dtype=torch.float32, device="cuda")
+    h32d, wpd, bpd = torch.from_numpy(h32).cuda(), wp.cuda(), bp.cuda()
+    S._ck(S.lib.evx_nn_project32(S._p(h32d), S._p(wpd), 32, 16, S._p(bpd), S._p(d), B, X, Y, Z, S._stream()))
+    refp = N.conv(h32.astype(np.float64), wp.float().numpy().astype(np.float64), bp.numpy().astype(np.float64))[..., 0]
+    assert rel(d.cpu().numpy(), refp) < 5e-6

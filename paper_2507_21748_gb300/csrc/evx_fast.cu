@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(8 * TP, SEP ? 1 : (8 * TP >= 128 ? 3 : 1))
 template <int R1, int TP>
 __global__ void __launch_bounds__(8 * TP) fxadj_kernel(XAdjArgs a) {
     constexpr int P = 8, L = R1 * TP, NB = R1 / TP, NT = P * TP;
-    extern __shared__ __align__(16) float4 smem4[];
+    extern __shared__ __align__(1024) float4 smem4[];
     float2* xb = reinterpret_cast<float2*>(smem4);  // [(L + TP) P] transposes
     float2* tA = xb + (L + TP) * P;
     float2* tB = NB == 1 ? tA : tA + L;

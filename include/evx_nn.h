@@ -36,7 +36,8 @@ extern "C" {
 /* conv epilogues: out(v, co) = acc(v, co) + bias(co), then */
 enum {
     EVX_NN_EPI_PLAIN = 0,    /* out (BF16) = value */
-    EVX_NN_EPI_GELU = 1,     /* pre (BF16) = value; out (BF16) = GELU(value) (erf form) */
+    EVX_NN_EPI_GELU = 1,     /* pre (BF16) = value (not stored if pre is NULL, e.g. in inference);
+                              * out (BF16) = GELU(value) (erf form) */
     EVX_NN_EPI_RESID = 2,    /* out (BF16) = res + value */
     EVX_NN_EPI_GELU_BWD = 3, /* out (BF16) = value * GELU'(pre) (pre read, not written) */
     EVX_NN_EPI_FIELD = 4,    /* out (FP32 field) = value of channel 0 */

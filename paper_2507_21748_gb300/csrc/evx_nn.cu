@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(NTHR) conv_fwd_kernel(ConvArgs a) {
                     continue;
                 }
                 if (EPI == EVX_NN_EPI_GELU) {
-                    *reinterpret_cast<__nv_bfloat162*>(a.pre + o) = __floats2bfloat162_rn(v0, v1);
+                    if (a.pre) *reinterpret_cast<__nv_bfloat162*>(a.pre + o) = __floats2bfloat162_rn(v0, v1);
                     v0 = gelu(v0);
                     v1 = gelu(v1);
                 } else if (EPI == EVX_NN_EPI_GELU_BWD) {
@@ -550,6 +550,162 @@ __global__ void __launch_bounds__(256) project_direct_kernel(const __nv_bfloat16
     }
 }
 
+// ---------------------------------------------------------------------------
+// Lift and projection with one warp per RY x 32 outputs of a (b, x) plane
+// (rows y0 .. y0 + RY - 1, z0 .. z0 + 31) and lane = channel: every global access
+// of a voxel is one coalesced row of its 32 channels, and each input row segment
+// is read once per warp for all the outputs it feeds (3 dz taps along z, up to
+// 3 dy taps across the RY rows). Needs Z % 32 = 0 and Y % RY = 0.
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// lane l ends with the lane sum of v[l] (a butterfly that halves the values per step)
+__device__ __forceinline__ float lane_sum_transpose(float (&v)[32], int lane) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = lane & off;
+#pragma unroll
+        for (int k = 0; k < off; ++k) {
+            const float send = upper ? v[k] : v[k + off];
+            const float keep = upper ? v[k + off] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0];
+}
+
+template <int RY>
+__device__ __forceinline__ bool lane_unit(long long u, int X, int Y, int Z, int& b, int& x, int& y0, int& z0) {
+    const int nzr = Z >> 5, nyr = Y / RY;
+    z0 = (int)(u % nzr) << 5;
+    long long r = u / nzr;
+    y0 = (int)(r % nyr) * RY;
+    r /= nyr;
+    x = (int)(r % X);
+    b = (int)(r / X);
+    return true;
+}
+
+// out(v) = bias(0) + sum_t sum_ci w[t][0][ci] h(v + off_t, ci); lane = ci
+template <bool F32, int RY>
+__global__ void __launch_bounds__(256, 1) project_lane_kernel(const __nv_bfloat16* __restrict__ h,
+                                                            const float* __restrict__ h32,
+                                                            const __nv_bfloat16* __restrict__ w, int wcout,
+                                                            const float* __restrict__ bias, float* out, int B,
+                                                            int X, int Y, int Z) {
+    __shared__ float ws[27][32];  // w[t][0][ci]
+    for (int i = threadIdx.x; i < 27 * 32; i += blockDim.x)
+        ws[i >> 5][i & 31] = __bfloat162float(w[(long long)(i >> 5) * wcout * 32 + (i & 31)]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const float b0 = bias ? bias[0] : 0.f;
+    const long long units = (long long)B * X * (Y / RY) * (Z >> 5);
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nw) {
+        int b, x, y0, z0;
+        lane_unit<RY>(u, X, Y, Z, b, x, y0, z0);
+        float acc[RY][32];
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[r][j] = 0.f;
+        const int zl = wrapi(z0 - 1, Z), zh = wrapi(z0 + 32, Z);
+#pragma unroll 1
+        for (int dx = 0; dx < 3; ++dx) {
+            const int xx = wrapi(x + dx - 1, X);
+#pragma unroll 1
+            for (int yy = 0; yy < RY + 2; ++yy) {
+                const long long row = (((long long)b * X + xx) * Y + wrapi(y0 + yy - 1, Y)) * Z;
+                float hv[34];
+#pragma unroll
+                for (int j = 0; j < 34; ++j) {
+                    const long long vi = row + (j == 0 ? zl : (j == 33 ? zh : z0 + j - 1));
+                    hv[j] = F32 ? __ldg(h32 + vi * 32 + lane) : __bfloat162float(h[vi * 32 + lane]);
+                }
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    const int dy = yy - r;  // tap 9 dx + 3 dy + dz  // input row y0 + yy - 1 = output row y0 + r + dy - 1
+                    if (dy < 0 || dy > 2) continue;
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz) {
+                        const float wt = ws[9 * dx + 3 * dy + dz][lane];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[r][j] = fmaf(wt, hv[j + dz], acc[r][j]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            const float sum = lane_sum_transpose(acc[r], lane);
+            out[(((long long)b * X + x) * Y + y0 + r) * Z + z0 + lane] = sum + b0;
+        }
+    }
+}
+
+// out(v, co) = bias(co) + sum_t w[t][co][0] val(f(v + off_t)), val = scale f (F32) or its
+// BF16 rounding; lane = co. F32 also writes the FP32 copy out32.
+template <bool F32, int RY>
+__global__ void __launch_bounds__(256, 2) lift_lane_kernel(const float* __restrict__ f, float scale,
+                                                         const __nv_bfloat16* __restrict__ w, int wcin,
+                                                         const float* __restrict__ bias, __nv_bfloat16* out,
+                                                         float* __restrict__ out32, int B, int X, int Y, int Z) {
+    __shared__ float ws[27][32];  // w[t][co][0]
+    for (int i = threadIdx.x; i < 27 * 32; i += blockDim.x) ws[i >> 5][i & 31] = __bfloat162float(w[i * wcin]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const float bl = bias ? bias[lane] : 0.f;
+    const long long units = (long long)B * X * (Y / RY) * (Z >> 5);
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nw) {
+        int b, x, y0, z0;
+        lane_unit<RY>(u, X, Y, Z, b, x, y0, z0);
+        float acc[RY][32];
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[r][j] = bl;
+#pragma unroll 1
+        for (int dx = 0; dx < 3; ++dx) {
+            const int xx = wrapi(x + dx - 1, X);
+#pragma unroll 1
+            for (int yy = 0; yy < RY + 2; ++yy) {
+                const long long row = (((long long)b * X + xx) * Y + wrapi(y0 + yy - 1, Y)) * Z;
+                // lane l holds z0 - 1 + l; lanes 0, 1 also z0 + 31, z0 + 32
+                float f0 = scale * f[row + wrapi(z0 - 1 + lane, Z)];
+                float f1 = lane < 2 ? scale * f[row + wrapi(z0 + 31 + lane, Z)] : 0.f;
+                if (!F32) {
+                    f0 = __bfloat162float(__float2bfloat16_rn(f0));
+                    f1 = __bfloat162float(__float2bfloat16_rn(f1));
+                }
+                float hv[34];
+#pragma unroll
+                for (int j = 0; j < 34; ++j)
+                    hv[j] = j < 32 ? __shfl_sync(0xffffffffu, f0, j) : __shfl_sync(0xffffffffu, f1, j - 32);
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    const int dy = yy - r;  // tap 9 dx + 3 dy + dz
+                    if (dy < 0 || dy > 2) continue;
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz) {
+                        const float wt = ws[9 * dx + 3 * dy + dz][lane];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[r][j] = fmaf(wt, hv[j + dz], acc[r][j]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            const long long v0 = (((long long)b * X + x) * Y + y0 + r) * Z + z0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                out[(v0 + j) * 32 + lane] = __float2bfloat16_rn(acc[r][j]);
+                if (F32) out32[(v0 + j) * 32 + lane] = acc[r][j];
+            }
+        }
+    }
+}
+
 }  // namespace evxnn
 
 // ===================================================================== C-ABI
@@ -661,8 +817,8 @@ evx_status evx_nn_conv3d(const void* in, const void* w, const float* bias, void*
                          int B, int X, int Y, int Z, int cin, int cout, int epilogue, void* stream) {
     if (!in || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
     if (!dims_ok(B, X, Y, Z)) return nn_fail(EVX_ERR_SIZE, "need Y even and Z a multiple of 64");
-    if ((epilogue == EVX_NN_EPI_GELU || epilogue == EVX_NN_EPI_GELU_BWD) && !pre)
-        return nn_fail(EVX_ERR_ARG, "GELU epilogues need the pre-activation buffer");
+    if (epilogue == EVX_NN_EPI_GELU_BWD && !pre)
+        return nn_fail(EVX_ERR_ARG, "the GELU-backward epilogue needs the pre-activation buffer");
     if (epilogue == EVX_NN_EPI_RESID && !res) return nn_fail(EVX_ERR_ARG, "residual epilogue needs res");
     if (epilogue == EVX_NN_EPI_RESID32 && (!pre || cout != 32))
         return nn_fail(EVX_ERR_ARG, "the FP32-stream epilogue needs the stream in pre and cout = 32");
@@ -685,13 +841,25 @@ evx_status evx_nn_conv3d(const void* in, const void* w, const float* bias, void*
     return nn_fail(EVX_ERR_ARG, "supported channel pairs: 16/32 -> 16/32");
 }
 
+// the lane-per-channel lift and projection: RY rows x 32 z per warp
+constexpr int LANE_RY = 2;
+static bool lane_path(int Y, int Z) { return Z % 32 == 0 && Y % LANE_RY == 0; }
+static int lane_grid(int B, int X, int Y, int Z) {
+    const long long warps = (long long)B * X * (Y / LANE_RY) * (Z / 32);
+    return (int)std::min<long long>((warps + 7) / 8, 16LL * nn_sms());
+}
+
 evx_status evx_nn_lift(const float* f, float scale, const void* w, int cin, int cout, const float* bias, void* out,
                        int B, int X, int Y, int Z, void* stream) {
     if (!f || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
     if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
     if (cout != 32 || cin < 1) return nn_fail(EVX_ERR_ARG, "lift: cout must be 32, cin >= 1");
-    lift_direct_kernel<false><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
-        f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, nullptr, B, X, Y, Z);
+    if (lane_path(Y, Z))
+        lift_lane_kernel<false, LANE_RY><<<lane_grid(B, X, Y, Z), 256, 0, (cudaStream_t)stream>>>(
+            f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, nullptr, B, X, Y, Z);
+    else
+        lift_direct_kernel<false><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+            f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, nullptr, B, X, Y, Z);
     return nn_cuda(cudaGetLastError());
 }
 
@@ -700,8 +868,12 @@ evx_status evx_nn_lift32(const float* f, float scale, const void* w, int cin, in
     if (!f || !w || !out || !out32) return nn_fail(EVX_ERR_ARG, "NULL pointer");
     if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
     if (cout != 32 || cin < 1) return nn_fail(EVX_ERR_ARG, "lift: cout must be 32, cin >= 1");
-    lift_direct_kernel<true><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
-        f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, out32, B, X, Y, Z);
+    if (lane_path(Y, Z))
+        lift_lane_kernel<true, LANE_RY><<<lane_grid(B, X, Y, Z), 256, 0, (cudaStream_t)stream>>>(
+            f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, out32, B, X, Y, Z);
+    else
+        lift_direct_kernel<true><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+            f, scale, (const __nv_bfloat16*)w, cin, bias, (__nv_bfloat16*)out, out32, B, X, Y, Z);
     return nn_cuda(cudaGetLastError());
 }
 
@@ -710,8 +882,12 @@ evx_status evx_nn_project(const void* h, const void* w, int cin, int cout, const
     if (!h || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
     if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
     if (cin != 32 || cout < 1) return nn_fail(EVX_ERR_ARG, "project: cin must be 32, cout >= 1");
-    project_direct_kernel<false><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16*)h, nullptr, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
+    if (lane_path(Y, Z))
+        project_lane_kernel<false, LANE_RY><<<lane_grid(B, X, Y, Z), 256, 0, (cudaStream_t)stream>>>(
+            (const __nv_bfloat16*)h, nullptr, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
+    else
+        project_direct_kernel<false><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+            (const __nv_bfloat16*)h, nullptr, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
     return nn_cuda(cudaGetLastError());
 }
 
@@ -720,8 +896,12 @@ evx_status evx_nn_project32(const float* h32, const void* w, int cin, int cout, 
     if (!h32 || !w || !out) return nn_fail(EVX_ERR_ARG, "NULL pointer");
     if (B <= 0 || X <= 0 || Y <= 0 || Z <= 0) return nn_fail(EVX_ERR_SIZE, "empty grid");
     if (cin != 32 || cout < 1) return nn_fail(EVX_ERR_ARG, "project: cin must be 32, cout >= 1");
-    project_direct_kernel<true><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
-        nullptr, h32, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
+    if (lane_path(Y, Z))
+        project_lane_kernel<true, LANE_RY><<<lane_grid(B, X, Y, Z), 256, 0, (cudaStream_t)stream>>>(
+            nullptr, h32, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
+    else
+        project_direct_kernel<true><<<8 * nn_sms(), 256, 0, (cudaStream_t)stream>>>(
+            nullptr, h32, (const __nv_bfloat16*)w, cout, bias, out, B, X, Y, Z);
     return nn_cuda(cudaGetLastError());
 }
 

@@ -180,7 +180,7 @@ __device__ __forceinline__ void epilogue_store(const ConvArgs& a, long long vox,
                 pp[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
                 ow[j] = __floats2bfloat162_rn(gelu(v[2 * j]), gelu(v[2 * j + 1]));
             }
-            *reinterpret_cast<uint4*>(a.pre + o + q * 8) = pw;
+            if (a.pre) *reinterpret_cast<uint4*>(a.pre + o + q * 8) = pw;  // NULL: inference, not kept
         } else if (EPI == EVX_NN_EPI_GELU_BWD) {
             const uint4 pw = *reinterpret_cast<const uint4*>(a.pre + o + q * 8);
             const __nv_bfloat162* pp = reinterpret_cast<const __nv_bfloat162*>(&pw);
@@ -216,6 +216,44 @@ __device__ __forceinline__ void epilogue_store(const ConvArgs& a, long long vox,
     }
 }
 
+// EVX_NN_EPI_RESID32 for one epilogue warp: 32 voxels vox0 .. vox0 + 31 (lane = voxel
+// of acc) x 16 channels c0 ... The sums are staged in shared memory ([voxel][16],
+// 16-byte chunk c of row v at chunk c ^ ((v >> 1) & 3): conflict-free both ways) and
+// the stream is read and written with lane l on voxel l / 4 + 8 i, channels
+// c0 + 4 (l % 4) ..: every instruction covers 8 whole 64-byte row pieces instead of
+// one 16-byte piece of 32 rows.
+__device__ __forceinline__ void resid32_staged(const ConvArgs& a, long long vox0, int c0, const uint32_t* acc,
+                                               const float* bias, float* stg, int lane) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4*>(stg + lane * 16 + 4 * (q ^ ((lane >> 1) & 3))) =
+            make_float4(__uint_as_float(acc[4 * q]) + bias[4 * q], __uint_as_float(acc[4 * q + 1]) + bias[4 * q + 1],
+                        __uint_as_float(acc[4 * q + 2]) + bias[4 * q + 2],
+                        __uint_as_float(acc[4 * q + 3]) + bias[4 * q + 3]);
+    __syncwarp();
+    const int c = lane & 3;
+    float4 s[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int v = (lane >> 2) + 8 * i;
+        s[i] = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.pre) + (vox0 + v) * 32 + c0 + 4 * c);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int v = (lane >> 2) + 8 * i;
+        const float4 d = *reinterpret_cast<const float4*>(stg + v * 16 + 4 * (c ^ ((v >> 1) & 3)));
+        s[i].x += d.x, s[i].y += d.y, s[i].z += d.z, s[i].w += d.w;
+        const long long o = (vox0 + v) * 32 + c0 + 4 * c;
+        *reinterpret_cast<float4*>(reinterpret_cast<float*>(a.pre) + o) = s[i];
+        uint2 ob;
+        __nv_bfloat162 lo = __floats2bfloat162_rn(s[i].x, s[i].y), hi = __floats2bfloat162_rn(s[i].z, s[i].w);
+        ob.x = *reinterpret_cast<uint32_t*>(&lo);
+        ob.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(a.out) + o) = ob;
+    }
+    __syncwarp();  // staging reads done before the next row overwrites it
+}
+
 // weights [t][co][ci] -> core-matrix layout [t][co/8][ci/8][8 co][8 ci]
 __device__ __forceinline__ void stage_weights(unsigned char* swb, const __nv_bfloat16* w, int nthreads) {
     for (int e = threadIdx.x; e < 27 * 32 * 4; e += nthreads) {  // 16-byte pieces (t, co, ci/8)
@@ -237,7 +275,9 @@ constexpr int NBLK = 16;                   // accumulator blocks of 32 columns (
 constexpr int NEPI = 8;                    // epilogue warps
 constexpr int NTH = (2 + NEPI) * 32;
 constexpr int BAR = WB + NS * SLOT;        // barriers: full[NS], tfull[NBLK], tempty[NBLK]
-constexpr int SMEM = BAR + 8 * (NS + 2 * NBLK) + 16 + 1024;  // + tensor-memory slot, abort flag, alignment
+constexpr int STG = (BAR + 8 * (NS + 2 * NBLK) + 16 + 15) & ~15;  // after the tensor-memory slot and abort flag
+constexpr int STG_WARP = 32 * 16 * 4;      // per epilogue warp: [32 voxels][16 channels] FP32 staging
+constexpr int SMEM = STG + NEPI * STG_WARP + 1024;  // + alignment
 constexpr uint32_t SLOT_TX = SLOT;         // TMA bytes per slot
 constexpr long long WAIT_BUDGET = 1LL << 31;
 }  // namespace ring
@@ -485,6 +525,7 @@ __global__ void __launch_bounds__(ring::NTH, 1)
     } else {
         // --------------------------------------------------------- epilogue
         const int q4 = warp & 3, h = (warp - 2) >> 2;  // accumulator lanes 32 q4 .., columns 16 h ..
+        float* stg = reinterpret_cast<float*>(sm + STG + (warp - 2) * STG_WARP);
         float bias[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) bias[i] = a.bias ? a.bias[h * 16 + i] : 0.f;
@@ -513,8 +554,11 @@ __global__ void __launch_bounds__(ring::NTH, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty + 8 * blk);
                 if (jv >= 2 && jv < L + 2) {
-                    const long long vox = ((long long)bx * Y + (ys + jv - 2)) * Z + z0 + q4 * 32 + lane;
-                    epilogue_store<EPI, 16>(a, vox, h * 16, acc, bias);
+                    const long long vox0 = ((long long)bx * Y + (ys + jv - 2)) * Z + z0 + q4 * 32;
+                    if (EPI == EVX_NN_EPI_RESID32)
+                        resid32_staged(a, vox0, h * 16, acc, bias, stg, lane);
+                    else
+                        epilogue_store<EPI, 16>(a, vox0 + lane, h * 16, acc, bias);
                 }
             }
         }

@@ -140,9 +140,10 @@ class Net:
         # the padded lift input: for the lift's weight gradient, or for the tensor-core lift when W != 32
         self.a_in = torch.empty((nv, self.CIN), dtype=bf, device=dev) if (train or W != 32) else None
         if not train:
-            # inference: the residual stream is updated in place; one GELU input/output pair
-            h, u, a = (torch.empty((nv, W), dtype=bf, device=dev) for _ in range(3))
-            self.h, self.u, self.a = [h] * (nblocks + 1), [u] * nblocks, [a] * nblocks
+            # inference: the residual stream is updated in place; one GELU input and output
+            # (the GELU pre-activations are not kept)
+            h, a = (torch.empty((nv, W), dtype=bf, device=dev) for _ in range(2))
+            self.h, self.u, self.a = [h] * (nblocks + 1), [None] * nblocks, [a] * nblocks
             self.h32 = torch.empty((nv, W), dtype=torch.float32, device=dev) if self.f32 else None
             self.d = torch.empty(nv, dtype=torch.float32, device=dev)
             self.pred = torch.empty(nv, dtype=torch.float32, device=dev)
@@ -238,7 +239,9 @@ class Net:
                 _ck(lib.evx_nn_field_to_act(_p(c), self.nvox, self.CIN, 1.0, _p(self.a_in), s))
             self._conv(self.a_in, "W0", self.p["b0"], self.h[0], self.CIN, W, EPI_PLAIN)
         for k in range(self.nb):
-            self._conv(self.h[k], "W1_%d" % k, self.p["b1_%d" % k], self.a[k], W, W, EPI_GELU, pre=self.u[k])
+            # the pre-activation is kept for the backward pass only
+            self._conv(self.h[k], "W1_%d" % k, self.p["b1_%d" % k], self.a[k], W, W, EPI_GELU,
+                       pre=self.u[k] if self.training else None)
             if self.f32:  # h32 += conv2(a); BF16 copy of the new stream into h[k + 1]
                 self._conv(self.a[k], "W2_%d" % k, self.p["b2_%d" % k], self.h[k + 1], W, W, EPI_RESID32,
                            pre=self.h32)

@@ -127,7 +127,7 @@ def test_conv_engine_setting(S):
     S.check()
 
 
-@pytest.mark.parametrize("shape", [(2, 4, 6, 64), (1, 3, 5, 7), (1, 1, 1, 9)])
+@pytest.mark.parametrize("shape", [(2, 4, 6, 64), (1, 3, 5, 7), (1, 1, 1, 9), (1, 1, 2, 32), (3, 2, 4, 96)])
 def test_direct_lift_and_projection(S, shape):
     """evx_nn_lift and evx_nn_project against the FP64 oracle's conv on the padded
     input / channel 0 of the output, and against the tensor-core convolutions
@@ -266,12 +266,16 @@ def test_training_beats_persistence_and_untrained(S):
     persist = float(np.mean([float(((x - y) ** 2).sum() / ((y - y.mean()) ** 2).sum()) ** 0.5
                              for x, y in zip(xs, ys)]))
     e0 = err(net)
-    hist = S.train(net, pool, 300, lr=2e-3, lr_final=2e-4)
+    # at lr 2e-3 -> 2e-4 these 300 steps are chaotic (held-out error 0.09 .. 0.52 of
+    # persistence over six network seeds, and rounding-level changes in the forward
+    # pass move a seed across that range); at 1e-3 -> 1e-4 every seed reached
+    # 0.037 .. 0.047 on the GB300
+    hist = S.train(net, pool, 300, lr=1e-3, lr_final=1e-4)
     e1 = err(net)
     pool.close()
     held.close()
     assert hist[-1] < 0.2 * hist[0]
-    assert e1 < 0.5 * persist and e1 < 0.5 * e0, (e1, persist, e0)
+    assert e1 < 0.2 * persist and e1 < 0.2 * e0, (e1, persist, e0)
 
 
 class _Perturbed:
@@ -353,11 +357,13 @@ def test_nonlinearity_scale_and_scaled_zero_mean_add(S):
 
 
 @pytest.mark.parametrize("engine", [0, 1])
-@pytest.mark.parametrize("shape", [(2, 4, 6, 64), (1, 3, 16, 128)])
+@pytest.mark.parametrize("shape", [(2, 4, 6, 64), (1, 3, 16, 128), (1, 2, 50, 128), (2, 2, 2, 256), (1, 1, 2, 128)])
 def test_conv_fp32_stream_epilogue(S, engine, shape):
     """EVX_NN_EPI_RESID32: the FP32 stream in `pre` is updated in place (stream +=
     conv + bias, within FP32 accumulation of the FP64 oracle's conv) and `out`
-    receives its BF16 copy; both engines."""
+    receives its BF16 copy; both engines (Z a multiple of 128: the pipelined
+    kernel, whose epilogue stages the sums through shared memory; Y = 50 gives
+    ragged y segments, X = 1 and Y = 2 wrap every neighbour onto the tile)."""
     import torch
     rng = np.random.default_rng(31 + engine + shape[2])
     x = bf16(rng.standard_normal(shape + (32,)))
@@ -383,12 +389,15 @@ def test_conv_fp32_stream_epilogue(S, engine, shape):
     assert torch.equal(out.cpu(), torch.from_numpy(got32).to(torch.bfloat16))
 
 
-def test_fp32_stream_lift_and_projection(S):
+@pytest.mark.parametrize("shape", [(2, 4, 6, 64), (1, 1, 2, 32), (1, 3, 5, 7), (2, 3, 4, 160)])
+def test_fp32_stream_lift_and_projection(S, shape):
     """evx_nn_lift32 (unrounded field, FP32 sums and their BF16 copy) and
-    evx_nn_project32 (reads the FP32 stream) against the FP64 oracle's conv."""
+    evx_nn_project32 (reads the FP32 stream) against the FP64 oracle's conv.
+    Z a multiple of 32 with Y even takes the lane-per-channel kernels (X = 1,
+    Y = 2, Z = 32 wraps every neighbour onto the warp's own rows), other sizes
+    the voxel-per-thread ones."""
     import torch
-    rng = np.random.default_rng(12)
-    shape = (2, 4, 6, 64)
+    rng = np.random.default_rng(12 + sum(shape))
     B, X, Y, Z = shape
     f = rng.uniform(-0.5, 0.5, shape).astype(np.float32)
     w0 = bf16(rng.standard_normal((27, 32, 16)) * 0.2)
@@ -411,3 +420,30 @@ def test_fp32_stream_lift_and_projection(S):
     S._ck(S.lib.evx_nn_project32(S._p(h32d), S._p(wpd), 32, 16, S._p(bpd), S._p(d), B, X, Y, Z, S._stream()))
     refp = N.conv(h32.astype(np.float64), wp.float().numpy().astype(np.float64), bp.numpy().astype(np.float64))[..., 0]
     assert rel(d.cpu().numpy(), refp) < 5e-6
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("shape", [(1, 3, 16, 128), (2, 4, 6, 64)])
+def test_gelu_epilogue_without_pre(S, engine, shape):
+    """EVX_NN_EPI_GELU with pre = NULL (inference) writes the same GELU output
+    and nothing else."""
+    import torch
+    rng = np.random.default_rng(77 + engine + shape[3])
+    x = bf16(rng.standard_normal(shape + (32,))).cuda()
+    w = bf16(rng.standard_normal((27, 32, 32)) * 0.1).cuda()
+    b = torch.from_numpy(rng.standard_normal(32).astype(np.float32)).cuda()
+    B, X, Y, Z = shape
+    outs = []
+    S.set_conv_engine(engine)
+    try:
+        for keep in (True, False):
+            out = torch.empty(shape + (32,), dtype=torch.bfloat16, device="cuda")
+            pre = torch.zeros(shape + (32,), dtype=torch.bfloat16, device="cuda")
+            S._ck(S.lib.evx_nn_conv3d(S._p(x), S._p(w), S._p(b), S._p(out), S._p(pre if keep else None), None,
+                                      B, X, Y, Z, 32, 32, S.EPI_GELU, S._stream()))
+            S.check()
+            outs.append((out, pre))
+    finally:
+        S.set_conv_engine(S.ENGINE_TCGEN05)
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1].abs().sum() > 0 and outs[1][1].abs().sum() == 0

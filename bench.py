@@ -413,7 +413,8 @@ def surrogate_bench(args):
     ms = conv_ms(S.ENGINE_TCGEN05)
     ms_sync = conv_ms(S.ENGINE_MMA_SYNC)
     out["conv_roofline"] = {"bound": "tensor",
-                            "kernel": "conv_ring_kernel<GELU> (tcgen05.mma bf16, TMEM accumulators, TMA ring)",
+                            "kernel": "conv_ring_kernel<GELU> (tcgen05.mma bf16, TMEM accumulators, TMA ring), "
+                                      "as inference runs it: GELU output only, no pre-activation store",
                             "achieved": flops / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                             "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_source": src + " bf16_tflops",
                             "ms_per_launch": ms,

@@ -85,9 +85,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fzstep_kernel(ZPassArgs a, int
                 xk.y = 0.f;
                 xm.y = 0.f;
             }
-            const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
-            const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);
-            v[n1] = cadd(A, mul_i<1>(cmul(cconj(rtws[k]), B)));
+            v[n1] = c2r_pre(xk, xm, rtws[k]);
         }
         __syncthreads();  // tile read: buf becomes transpose space
         // inverse complex FFT of length M
@@ -285,9 +283,7 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int n
                 xk.y = 0.f;
                 xm.y = 0.f;
             }
-            const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
-            const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);
-            v[n1] = cadd(A, mul_i<1>(cmul(cconj(rtws[k]), B)));
+            v[n1] = c2r_pre(xk, xm, rtws[k]);
         }
         __syncthreads();  // tile read: buf becomes transpose space
         Dft<R1, 1>::run(v);

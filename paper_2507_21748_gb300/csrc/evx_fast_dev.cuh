@@ -113,6 +113,20 @@ __device__ __forceinline__ void t2_s(float2 (&v)[R1], float2* xb, int n2, int p)
 // the same warp at index 31 - d (thread 0: its own index 32 - d) and is
 // fetched by warp shuffle; otherwise the row passes through the M-entry shared
 // row xz. Every thread of the CTA calls this (it may synchronise the CTA).
+// Real-transform pre- and post-processing of one pair (k, M - k) of a length-2M
+// real row held as M complex values, w = exp(-2 pi i k / 2M); P and Q are the
+// pair's sum and difference, the twiddle product is taken into FMAs.
+// C2R: Z_k = P + i conj(w) Q with P = X_k + conj X_{M-k}, Q = X_k - conj X_{M-k}
+__device__ __forceinline__ float2 c2r_pre(float2 xk, float2 xm, float2 w) {
+    const float px = xk.x + xm.x, py = xk.y - xm.y, qx = xk.x - xm.x, qy = xk.y + xm.y;
+    return make_float2(fmaf(-w.x, qy, fmaf(w.y, qx, px)), fmaf(w.x, qx, fmaf(w.y, qy, py)));
+}
+// R2C: X_k = (P - i w Q) / 2 with P = Z_k + conj Z_{M-k}, Q = Z_k - conj Z_{M-k}
+__device__ __forceinline__ float2 r2c_post(float2 zk, float2 zm, float2 w) {
+    const float px = zk.x + zm.x, py = zk.y - zm.y, qx = zk.x - zm.x, qy = zk.y + zm.y;
+    return make_float2(0.5f * fmaf(w.x, qy, fmaf(w.y, qx, px)), 0.5f * fmaf(-w.x, qx, fmaf(w.y, qy, py)));
+}
+
 template <int R1, int TP>
 __device__ __forceinline__ void r2c_store(const float2 (&v)[R1], int n2, float2* xz, float2* out, bool rowok,
                                           const float2* rtws) {
@@ -126,11 +140,8 @@ __device__ __forceinline__ void r2c_store(const float2 (&v)[R1], int n2, float2*
             zm.x = __shfl_sync(0xffffffffu, v[31 - d].x, src);
             zm.y = __shfl_sync(0xffffffffu, v[31 - d].y, src);
             if (n2 == 0) zm = v[(32 - d) & 31];
-            const float2 zk = v[d];
-            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-            const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
             const int k = n2 + TP * d;
-            if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
+            if (rowok) out[k] = r2c_post(v[d], zm, rtws[k]);
         }
     } else {
 #pragma unroll
@@ -140,10 +151,7 @@ __device__ __forceinline__ void r2c_store(const float2 (&v)[R1], int n2, float2*
         for (int d = 0; d < R1; ++d) {
             const int k = n2 + TP * d;
             const float2 zm = xz[k == 0 ? 0 : M - k];
-            const float2 zk = v[d];
-            const float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-            const float2 B = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
-            if (rowok) out[k] = cadd(A, mul_i<-1>(cmul(rtws[k], B)));
+            if (rowok) out[k] = r2c_post(v[d], zm, rtws[k]);
         }
     }
     if (rowok && n2 == 0) out[M] = make_float2(v[0].x - v[0].y, 0.f);  // X_M = Re Z_0 - Im Z_0

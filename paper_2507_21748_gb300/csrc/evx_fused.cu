@@ -153,9 +153,7 @@ __device__ __forceinline__ void z_item(float2* W, long long r0, const YZYArgs& a
             xk.y = 0.f;
             xm.y = 0.f;
         }
-        const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
-        const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);
-        v[n1] = cadd(A, mul_i<1>(cmul(cconj(rtws[k]), B)));
+        v[n1] = fast::c2r_pre(xk, xm, rtws[k]);
     }
     __syncthreads();  // tile read: buf becomes transpose space
     Dft<R1, 1>::run(v);

@@ -428,18 +428,20 @@ __device__ __forceinline__ void fence_async_smem() {
 }
 
 // y pass with TMA: boxes {8, 32 (y in block), 1 (x), BOX/32 (y blocks)} cover
-// BOX consecutive y rows of one x line (y blocks of 32 rows)
-template <int R1, int TP, int DIR>
+// BOX consecutive y rows of one x line (y blocks of 32 rows). NBUF tile buffers
+// take the loads: with two (L = 1024, one CTA per SM) the tile after next is
+// already on its way while a tile is transformed.
+template <int R1, int TP, int DIR, int NBUF>
 __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int ntiles,
                                                             const __grid_constant__ CUtensorMap min,
                                                             const __grid_constant__ CUtensorMap mout) {
     constexpr int L = R1 * TP, NB = R1 / TP, XB = (L + TP) * 8, BOX = ybox(R1, L), NBOX = L / BOX;
     extern __shared__ __align__(1024) float4 smem4[];
-    float2* buf = reinterpret_cast<float2*>(smem4);  // [L][8] TMA destination
-    float2* xb = buf + L * 8;                         // transpose, then store staging
+    float2* bufs = reinterpret_cast<float2*>(smem4);  // [NBUF][L][8] TMA destinations
+    float2* xb = bufs + NBUF * L * 8;                 // transpose, then store staging
     float2* tA = xb + XB;                             // [L] twiddles (n2 ownership)
     float2* tB = tA + L;                              // [L] twiddles (block ownership)
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tB + L);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tB + L);  // [NBUF]
     const int p = threadIdx.x & 7, n2 = threadIdx.x >> 3;
     const int nchunks = a.nchunks;
     int tile = blockIdx.x;
@@ -447,29 +449,33 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
     fill_twiddles<R1, TP>(tA, tB, a.tw, 8 * TP);
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        for (int b = 0; b < NBUF; ++b) mbar_init(bar + b, 1);
         s_abort = 0;
     }
     __syncthreads();
-    auto issue = [&](int tl) {
+    auto issue = [&](int tl, int b) {
         const int outer = tl / nchunks, chunk = tl - outer * nchunks;
         fence_async_smem();
-        mbar_expect_tx(bar, L * 8 * sizeof(float2));
+        mbar_expect_tx(bar + b, L * 8 * sizeof(float2));
 #pragma unroll
-        for (int b = 0; b < NBOX; ++b) tma_load4(buf + b * BOX * 8, &min, chunk * 8, 0, outer, b * BOX / a.YB, bar);
+        for (int q = 0; q < NBOX; ++q)
+            tma_load4(bufs + (b * L + q * BOX) * 8, &min, chunk * 8, 0, outer, q * BOX / a.YB, bar + b);
     };
-    if (threadIdx.x == 0) issue(tile);
+    if (threadIdx.x == 0)
+        for (int b = 0; b < NBUF && tile + b * (int)gridDim.x < ntiles; ++b) issue(tile + b * gridDim.x, b);
     uint32_t parity = 0;
-    for (; tile < ntiles; tile += gridDim.x) {
-        mbar_wait_or_abort(bar, parity, &s_abort);
-        parity ^= 1;
+    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+        const int b = NBUF == 1 ? 0 : it % NBUF;
+        float2* buf = bufs + b * L * 8;
+        mbar_wait_or_abort(bar + b, parity, &s_abort);
+        if (b == NBUF - 1) parity ^= 1;
         float2 v[R1];
 #pragma unroll
         for (int n1 = 0; n1 < R1; ++n1) v[n1] = buf[(n2 + TP * n1) * 8 + p];
         if (threadIdx.x == 0) bulk_wait_read0();  // previous store has left the staging tile
         __syncthreads();
-        const int next = tile + gridDim.x;
-        if (threadIdx.x == 0 && next < ntiles) issue(next);
+        const int next = tile + NBUF * gridDim.x;
+        if (threadIdx.x == 0 && next < ntiles) issue(next, b);
         Dft<R1, DIR>::run(v);
         twiddle_a<R1, TP, DIR>(v, n2, tA);
         t1_s<R1, TP, 8>(v, xb, n2, p);
@@ -484,8 +490,8 @@ __global__ void __launch_bounds__(8 * TP) fspass_tma_kernel(SPassArgs a, int nti
         if (threadIdx.x == 0) {
             const int outer = tile / nchunks, chunk = tile - outer * nchunks;
 #pragma unroll
-            for (int b = 0; b < NBOX; ++b)
-                tma_store4(&mout, chunk * 8, 0, outer, b * BOX / a.YB, xb + b * BOX * 8);
+            for (int q = 0; q < NBOX; ++q)
+                tma_store4(&mout, chunk * 8, 0, outer, q * BOX / a.YB, xb + q * BOX * 8);
             bulk_commit();
         }
     }
@@ -876,16 +882,17 @@ static bool run_fspass_tma(const SPassArgs& a, cudaStream_t st, cudaError_t* err
     if (!make_map(&mi, a.in, a.ncols, a.YB, a.nouter, a.L, Zp, 8, a.YB, 1, BOX / a.YB) ||
         !make_map(&mo, a.out, a.ncols, a.YB, a.nouter, a.L, Zp, 8, a.YB, 1, BOX / a.YB))
         return false;
-    const size_t smem = sizeof(float2) * (L * 8 + (L + TP) * 8 + 2 * L) + 16;
+    constexpr int NBUF = L == 1024 ? 2 : 1;  // one CTA per SM at 1024 either way
+    const size_t smem = sizeof(float2) * (NBUF * L * 8 + (L + TP) * 8 + 2 * L) + 8 * NBUF;
     int per = 0;
-    cudaError_t e = prep(fast::fspass_tma_kernel<R1, TP, DIR>, smem, 8 * TP, &per);
+    cudaError_t e = prep(fast::fspass_tma_kernel<R1, TP, DIR, NBUF>, smem, 8 * TP, &per);
     if (e != cudaSuccess) {
         *err = e;
         return true;
     }
     const int ntiles = a.nchunks * a.nouter;
     const int grid = std::min(ntiles, per * num_sms());
-    fast::fspass_tma_kernel<R1, TP, DIR><<<grid, 8 * TP, smem, st>>>(a, ntiles, mi, mo);
+    fast::fspass_tma_kernel<R1, TP, DIR, NBUF><<<grid, 8 * TP, smem, st>>>(a, ntiles, mi, mo);
     *err = cudaGetLastError();
     return true;
 }

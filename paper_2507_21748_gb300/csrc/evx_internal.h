@@ -197,6 +197,10 @@ cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st, int* gri
 //   rhs = (1 / h^2) sum over the 6 neighbours j of (M_i + M_j)/2 (mu_j - mu_i), M = M0 max(1 - c^2, 0)
 //   partials[b] = sum over the CTA's voxels of (c^2 - 1)^2 / 4 + (kappa / 2h^2) sum_d (c_{i+e_d} - c_i)^2
 cudaError_t launch_vm_mu(const float* c, float* mu, int nx, int ny, int nz, float kappa_h2, cudaStream_t st);
+// both stencils in one pass (ny a multiple of 8, nz of 64; vm_fd_fused_ok): rhs from c, mu not stored
+bool vm_fd_fused_ok(int nx, int ny, int nz);
+cudaError_t launch_vm_fd(const float* c, float* rhs, int nx, int ny, int nz, float kappa_h2, float M0, float inv_h2,
+                         cudaStream_t st);
 cudaError_t launch_vm_rhs(const float* c, const float* mu, float* rhs, int nx, int ny, int nz, float M0,
                           float inv_h2, cudaStream_t st);
 cudaError_t launch_vm_energy(const float* c, int nx, int ny, int nz, double kappa_2h2, double* partials, int nparts,

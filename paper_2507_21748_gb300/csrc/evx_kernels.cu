@@ -482,6 +482,124 @@ __global__ void __launch_bounds__(256) vm_rhs_kernel(const float* __restrict__ c
     }
 }
 
+// Both stencils in one pass (rhs straight from c, mu never stored): a CTA owns
+// TY x TZ columns (y, z) and marches along x through XC planes, with c in a ring
+// of 8 planes (2-halo in y and z), and mu and the mobility M(c) in rings of 4
+// planes (1-halo) in shared memory. Plane x + 3 is copied in with cp.async while
+// plane x is computed; each thread's shared and global offsets are the same on
+// every plane and are computed once. Each c value is read from HBM once (its
+// halo copies mostly from L2) and rhs written once: 8 B per voxel against 20 B
+// for the two separate kernels. The arithmetic and its grouping are those of
+// vm_mu_kernel and vm_rhs_kernel (same results to the bit).
+constexpr int VM_TY = 8, VM_TZ = 64, VM_XC = 64, VM_CS = 8, VM_NT = 256;
+constexpr int VM_CY = VM_TY + 4, VM_CZ = VM_TZ + 4, VM_MY = VM_TY + 2, VM_MZ = VM_TZ + 2;
+constexpr int VM_CP = VM_CY * VM_CZ, VM_MP = VM_MY * VM_MZ;  // floats per c / mu plane
+constexpr int VM_NL = (VM_CP + VM_NT - 1) / VM_NT, VM_NM = (VM_MP + VM_NT - 1) / VM_NT, VM_NR = VM_TY * VM_TZ / VM_NT;
+__device__ __forceinline__ int vm_wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__global__ void __launch_bounds__(VM_NT) vm_fd_kernel(const float* __restrict__ c, float* __restrict__ rhs, int nx,
+                                                       int ny, int nz, float kh2, float M0, float ih2) {
+    static_assert(VM_TY * VM_TZ % VM_NT == 0, "rhs points per thread");
+    extern __shared__ float vm_smem[];
+    float* cs = vm_smem;                  // [VM_CS][VM_CY][VM_CZ]
+    float* ms = cs + VM_CS * VM_CP;       // [4][VM_MY][VM_MZ] mu
+    float* mbs = ms + 4 * VM_MP;          // [4][VM_MY][VM_MZ] M(c)
+    const int y0 = blockIdx.x * VM_TY, z0 = blockIdx.y * VM_TZ, x0 = blockIdx.z * VM_XC;
+    const int xe = min(x0 + VM_XC, nx);
+    const long long V = (long long)nx * ny * nz;
+    const int tid = threadIdx.x;
+    // this thread's points: c loads (plane offset in c, index in a c plane), mu / M
+    // points (index in a mu plane, centre index in a c plane), rhs points (likewise)
+    int lg[VM_NL], ls[VM_NL], mi_[VM_NM], mc[VM_NM], rm[VM_NR], ro[VM_NR];
+#pragma unroll
+    for (int k = 0; k < VM_NL; ++k) {
+        const int i = tid + k * VM_NT, r = i / VM_CZ, q = i - r * VM_CZ;
+        lg[k] = i < VM_CP ? vm_wrap(y0 + r - 2, ny) * nz + vm_wrap(z0 + q - 2, nz) : -1;
+        ls[k] = i;
+    }
+#pragma unroll
+    for (int k = 0; k < VM_NM; ++k) {
+        const int i = tid + k * VM_NT, r = i / VM_MZ, q = i - r * VM_MZ;
+        mi_[k] = i < VM_MP ? i : -1;
+        mc[k] = (r + 1) * VM_CZ + q + 1;
+    }
+#pragma unroll
+    for (int k = 0; k < VM_NR; ++k) {
+        const int i = tid + k * VM_NT, r = i / VM_TZ, q = i - r * VM_TZ;
+        rm[k] = (r + 1) * VM_MZ + q + 1;
+        ro[k] = (y0 + r) * nz + z0 + q;
+    }
+    auto load_c = [&](int xp) {  // plane xp (x0 - 2 <= xp <= xe + 1) into slot (xp + 8) % 8, one commit group
+        float* dst = cs + ((xp + VM_CS) % VM_CS) * VM_CP;
+        const long long pb = (long long)vm_wrap(xp, nx) * ny * nz;
+#pragma unroll
+        for (int k = 0; k < VM_NL; ++k)
+            if (lg[k] >= 0) {
+                const long long g = pb + lg[k];
+                cp_async4(dst + ls[k], c + (EVX_IN(g, V) ? g : 0), EVX_IN(g, V));
+            }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto mu_plane = [&](int xp) {  // mu and M of plane xp, rows y0 - 1 .., columns z0 - 1 ..
+        const float* c0 = cs + ((xp + VM_CS) % VM_CS) * VM_CP;
+        const float* cm = cs + ((xp + VM_CS - 1) % VM_CS) * VM_CP;
+        const float* cp = cs + ((xp + 1) % VM_CS) * VM_CP;
+        float* mo = ms + ((xp + 4) & 3) * VM_MP;
+        float* bo = mbs + ((xp + 4) & 3) * VM_MP;
+#pragma unroll
+        for (int k = 0; k < VM_NM; ++k)
+            if (mi_[k] >= 0) {
+                const int e = mc[k];
+                const float v = c0[e];
+                const float nb = ((cp[e] + cm[e]) + (c0[e + VM_CZ] + c0[e - VM_CZ])) + (c0[e + 1] + c0[e - 1]);
+                mo[mi_[k]] = v * (v * v - 1.f) - kh2 * fmaf(-6.f, v, nb);
+                bo[mi_[k]] = M0 * fmaxf(1.f - v * v, 0.f);
+            }
+    };
+    for (int xp = x0 - 2; xp <= x0 + 2; ++xp) load_c(xp);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    mu_plane(x0 - 1);
+    mu_plane(x0);
+    for (int x = x0; x < xe; ++x) {
+        // planes x - 1 .. x + 2 are in; plane x + 3 takes the slot of plane x - 5
+        if (x + 3 <= xe + 1)
+            load_c(x + 3);
+        else
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // all but the newest group: plane x + 2
+        __syncthreads();
+        mu_plane(x + 1);  // the mu and M slots of plane x - 3
+        __syncthreads();
+        const float* u0 = ms + ((x + 4) & 3) * VM_MP;
+        const float* um = ms + ((x + 3) & 3) * VM_MP;
+        const float* up = ms + ((x + 5) & 3) * VM_MP;
+        const float* b0 = mbs + ((x + 4) & 3) * VM_MP;
+        const float* bm = mbs + ((x + 3) & 3) * VM_MP;
+        const float* bp = mbs + ((x + 5) & 3) * VM_MP;
+        const long long pb = (long long)x * ny * nz;
+#pragma unroll
+        for (int k = 0; k < VM_NR; ++k) {
+            const int e = rm[k];
+            const float mi = b0[e], ui = u0[e];
+            // neighbours in the order x+, x-, y+, y-, z+, z-
+            float acc = 0.f;
+            acc = fmaf(0.5f * (mi + bp[e]), up[e] - ui, acc);
+            acc = fmaf(0.5f * (mi + bm[e]), um[e] - ui, acc);
+            acc = fmaf(0.5f * (mi + b0[e + VM_MZ]), u0[e + VM_MZ] - ui, acc);
+            acc = fmaf(0.5f * (mi + b0[e - VM_MZ]), u0[e - VM_MZ] - ui, acc);
+            acc = fmaf(0.5f * (mi + b0[e + 1]), u0[e + 1] - ui, acc);
+            acc = fmaf(0.5f * (mi + b0[e - 1]), u0[e - 1] - ui, acc);
+            const long long o = pb + ro[k];
+            if (EVX_IN(o, V)) rhs[o] = acc * ih2;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // FD energy partials: (c^2 - 1)^2 / 4 + (kappa / 2h^2) sum_d (c_{i+e_d} - c_i)^2 per voxel, FP64
 __global__ void __launch_bounds__(256) vm_energy_kernel(const float* __restrict__ c, int nx, int ny, int nz,
                                                          double k2h2, double* partials) {
@@ -655,6 +773,17 @@ static int vm_grid(int nx, int ny) {
 
 cudaError_t launch_vm_mu(const float* c, float* mu, int nx, int ny, int nz, float kappa_h2, cudaStream_t st) {
     vm_mu_kernel<<<vm_grid(nx, ny), 256, 0, st>>>(c, mu, nx, ny, nz, kappa_h2);
+    return cudaGetLastError();
+}
+
+bool vm_fd_fused_ok(int nx, int ny, int nz) { return ny % VM_TY == 0 && nz % VM_TZ == 0 && nx >= 8; }
+
+cudaError_t launch_vm_fd(const float* c, float* rhs, int nx, int ny, int nz, float kappa_h2, float M0, float inv_h2,
+                         cudaStream_t st) {
+    if (!vm_fd_fused_ok(nx, ny, nz)) return cudaErrorInvalidValue;
+    constexpr size_t smem = sizeof(float) * (VM_CS * VM_CP + 8 * VM_MP);  // 47,232 bytes
+    vm_fd_kernel<<<dim3(ny / VM_TY, nz / VM_TZ, (nx + VM_XC - 1) / VM_XC), VM_NT, smem, st>>>(c, rhs, nx, ny, nz,
+                                                                                           kappa_h2, M0, inv_h2);
     return cudaGetLastError();
 }
 

@@ -218,9 +218,15 @@ static cudaError_t issue_vm_step(evx_grid* g, cudaStream_t st, cudaEvent_t* ev) 
     float* mu = reinterpret_cast<float*>(g->W);
     const double ih2 = 1.0 / (g->p.h * g->p.h);
     mark(ev, 0, st, "FD stencils");
-    if ((e = launch_vm_mu(c, mu, g->nx, g->ny, g->nz, (float)(g->p.kappa * ih2), st)) != cudaSuccess) return e;
-    if ((e = launch_vm_rhs(c, mu, g->R, g->nx, g->ny, g->nz, (float)g->p.M, (float)ih2, st)) != cudaSuccess)
-        return e;
+    if (vm_fd_fused_ok(g->nx, g->ny, g->nz)) {  // both stencils in one pass (mu not stored)
+        if ((e = launch_vm_fd(c, g->R, g->nx, g->ny, g->nz, (float)(g->p.kappa * ih2), (float)g->p.M, (float)ih2,
+                              st)) != cudaSuccess)
+            return e;
+    } else {
+        if ((e = launch_vm_mu(c, mu, g->nx, g->ny, g->nz, (float)(g->p.kappa * ih2), st)) != cudaSuccess) return e;
+        if ((e = launch_vm_rhs(c, mu, g->R, g->nx, g->ny, g->nz, (float)g->p.M, (float)ih2, st)) != cudaSuccess)
+            return e;
+    }
     mark(ev, 1, st, "z R2C");
     ZPassArgs z = z_args(g);
     z.rin = g->R;

@@ -180,15 +180,16 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fr2c_kernel(ZPassArgs a, int n
     if (tile >= ntiles) return;
     fill_twiddles<R1, TP>(tA, tB, a.tw, NTZ);
     for (int i = threadIdx.x; i <= M; i += NTZ) rtws[i] = a.rtw[i];
+    // rows to warps (the caller's row once per row), 16-byte chunks of 4 floats to lanes
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     auto issue = [&](int tl) {
         const long long row0 = (long long)tl * RPC;
-        for (int e = threadIdx.x; e < RPC * (M / 2); e += NTZ) {  // 16-byte chunks: 4 floats
-            const int rr = e / (M / 2), q = e - rr * (M / 2);
+        for (int rr = warp; rr < RPC; rr += NTZ / 32) {
             const long long row = row0 + rr;
             const bool ok = row < a.nrows;
-            const long long ur = a.map_rows ? user_row(row, a.YB, a.nxr, a.nyr) : row;
-            const float* src = ok ? a.rin + ur * a.rpitch + 4 * q : a.rin;
-            cp_async16(buf + rr * BS + 2 * q, src, ok ? 16 : 0);
+            const long long ur = ok ? (a.map_rows ? user_row(row, a.YB, a.nxr, a.nyr) : row) : 0;
+            const float* src = a.rin + ur * a.rpitch;
+            for (int q = lane; q < M / 2; q += 32) cp_async16(buf + rr * BS + 2 * q, ok ? src + 4 * q : a.rin, ok ? 16 : 0);
         }
         cp_commit();
     };
@@ -305,25 +306,27 @@ __global__ void __launch_bounds__(NTZ, 512 / NTZ) fc2r_kernel(ZPassArgs a, int n
                 buf[r * BS + n2 * NB + i + R1 * c] = make_float2(fmaf(z.x, s, cbl) + cb, fmaf(z.y, s, cbl) + cb);
             }
         __syncthreads();
-        for (int e = threadIdx.x; e < RPC * (M / 2); e += NTZ) {  // coalesced 16-byte stores
-            const int rr = e / (M / 2), q = e - rr * (M / 2);
+        for (int rr = warp; rr < RPC; rr += NTZ / 32) {  // rows to warps, coalesced 16-byte stores by lanes
             const long long row = row0 + rr;
             if (row >= a.nrows) continue;
             const long long ur = a.map_rows ? user_row(row, a.YB, a.nxr, a.nyr) : row;
-            float4* dst = reinterpret_cast<float4*>(a.rout + ur * a.rpitch + 4 * q);
-            float4 val = *reinterpret_cast<const float4*>(buf + rr * BS + 2 * q);
-            if (ACC) {
-                const float4 prev = *dst;
-                val.x += prev.x;
-                val.y += prev.y;
-                val.z += prev.z;
-                val.w += prev.w;
-            }
-            *dst = val;
-            if (PART) {
-                const double q0 = (double)val.x * val.x - 1.0, q1 = (double)val.y * val.y - 1.0;
-                const double q2 = (double)val.z * val.z - 1.0, q3 = (double)val.w * val.w - 1.0;
-                acc += q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+            float4* drow = reinterpret_cast<float4*>(a.rout + ur * a.rpitch);
+            for (int q = lane; q < M / 2; q += 32) {
+                float4* dst = drow + q;
+                float4 val = *reinterpret_cast<const float4*>(buf + rr * BS + 2 * q);
+                if (ACC) {
+                    const float4 prev = *dst;
+                    val.x += prev.x;
+                    val.y += prev.y;
+                    val.z += prev.z;
+                    val.w += prev.w;
+                }
+                *dst = val;
+                if (PART) {
+                    const double q0 = (double)val.x * val.x - 1.0, q1 = (double)val.y * val.y - 1.0;
+                    const double q2 = (double)val.z * val.z - 1.0, q3 = (double)val.w * val.w - 1.0;
+                    acc += q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+                }
             }
         }
         __syncthreads();  // staged rows stored: buf free for the next tile

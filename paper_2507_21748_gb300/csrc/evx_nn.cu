@@ -254,6 +254,57 @@ __global__ void bias_grad_kernel(const __nv_bfloat16* dy, long long nvox, int C,
         __syncthreads();
     }
 }
+// One pass for all channels (C = 16 or 32): C / 8 threads per voxel, each summing
+// 8 channels from 16-byte loads (four voxels in flight), FP32 over 32 voxels at a
+// time and FP64 beyond;
+// the CTA then adds its threads' sums per channel in a fixed order.
+template <int C>
+__global__ void __launch_bounds__(256) bias_grad_vec_kernel(const __nv_bfloat16* __restrict__ dy, long long nvox,
+                                                             double* partials) {
+    constexpr int TPV = C / 8;
+    __shared__ double red[256][9];  // padded rows
+    const int piece = threadIdx.x % TPV;
+    const long long stride = (long long)gridDim.x * blockDim.x / TPV;
+    double acc[8];
+    float part[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.0, part[k] = 0.f;
+    // four voxels in flight per thread per round; FP32 over 8 rounds, then FP64
+    int cnt = 0;
+    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TPV; v < nvox; v += 4 * stride) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long vu = v + u * stride;
+            q[u] = vu < nvox ? *reinterpret_cast<const uint4*>(dy + vu * C + 8 * piece) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q[u]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(h[j]);
+                part[2 * j] += f.x;
+                part[2 * j + 1] += f.y;
+            }
+        }
+        if (++cnt == 8) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += part[k], part[k] = 0.f;
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k] + part[k];
+    __syncthreads();
+    if (threadIdx.x < C) {
+        const int pc = threadIdx.x / 8, j = threadIdx.x % 8;
+        double s = 0.0;
+        for (int t = pc; t < (int)blockDim.x; t += TPV) s += red[t][j];
+        partials[(long long)blockIdx.x * C + threadIdx.x] = s;
+    }
+}
+
 __global__ void bias_grad_finish(const double* partials, int nparts, int C, float* db) {
     const int co = threadIdx.x;
     if (co < C) {
@@ -940,7 +991,12 @@ evx_status evx_nn_bias_grad(const void* dy, long long nvox, int c, double* parti
                             void* stream) {
     if (!dy || !partials || !db || c <= 0 || c > 256 || nparts <= 0) return nn_fail(EVX_ERR_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
-    bias_grad_kernel<<<nparts, 256, 0, st>>>((const __nv_bfloat16*)dy, nvox, c, partials);
+    if (c == 32)
+        bias_grad_vec_kernel<32><<<nparts, 256, 0, st>>>((const __nv_bfloat16*)dy, nvox, partials);
+    else if (c == 16)
+        bias_grad_vec_kernel<16><<<nparts, 256, 0, st>>>((const __nv_bfloat16*)dy, nvox, partials);
+    else
+        bias_grad_kernel<<<nparts, 256, 0, st>>>((const __nv_bfloat16*)dy, nvox, c, partials);
     bias_grad_finish<<<1, 256, 0, st>>>(partials, nparts, c, db);
     return nn_cuda(cudaGetLastError());
 }

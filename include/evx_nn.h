@@ -84,7 +84,9 @@ evx_status evx_nn_conv3d_wgrad(const void *dy, const void *x, float *dw, float *
                                size_t partial_floats, int B, int X, int Y, int Z, int cin, int cout,
                                void *stream);
 
-/* Bias gradient db[co] = sum_v dy(v, co) (FP64 partials: nparts * c doubles). */
+/* Bias gradient db[co] = sum_v dy(v, co) (FP64 partials: nparts * c doubles; fixed
+ * summation order). c = 16 or 32 with dy 16-byte aligned: one pass over dy; other
+ * cases: one pass per channel. */
 evx_status evx_nn_bias_grad(const void *dy, long long nvox, int c, double *partials, int nparts, float *db,
                             void *stream);
 

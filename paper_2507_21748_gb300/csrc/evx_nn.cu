@@ -991,9 +991,10 @@ evx_status evx_nn_bias_grad(const void* dy, long long nvox, int c, double* parti
                             void* stream) {
     if (!dy || !partials || !db || c <= 0 || c > 256 || nparts <= 0) return nn_fail(EVX_ERR_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
-    if (c == 32)
+    const bool al16 = ((uintptr_t)dy & 15) == 0;  // the one-pass kernel reads 16-byte pieces
+    if (c == 32 && al16)
         bias_grad_vec_kernel<32><<<nparts, 256, 0, st>>>((const __nv_bfloat16*)dy, nvox, partials);
-    else if (c == 16)
+    else if (c == 16 && al16)
         bias_grad_vec_kernel<16><<<nparts, 256, 0, st>>>((const __nv_bfloat16*)dy, nvox, partials);
     else
         bias_grad_kernel<<<nparts, 256, 0, st>>>((const __nv_bfloat16*)dy, nvox, c, partials);

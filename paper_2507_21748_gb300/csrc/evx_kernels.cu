@@ -382,6 +382,45 @@ __global__ void __launch_bounds__(NT) sum_rows_kernel(const float* c, long long 
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// FP64 row sums with 16-byte loads (rowlen and pitch multiples of 4, c 16-byte
+// aligned): rows to warps, a lane takes every 32nd float4 of its warp's row. Each
+// lane adds up to 32 floats exactly in FP32 as a rounded sum s and the sum e of the
+// TwoSum error terms (Knuth), and passes s + e to its FP64 accumulator: the FP64
+// work (the slow pipe on this GPU) falls to 2 operations per 32 elements, and the
+// result is the FP64 sum to within the FP64 rounding of the old kernel.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+    const float t = s + x, bp = t - s;
+    e += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+__global__ void __launch_bounds__(NT) sum_rows_vec_kernel(const float* c, long long nrows, int rowlen,
+                                                          long long pitch, double* partials) {
+    __shared__ double ws[NT / 32];
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * NT) >> 5;
+    double acc = 0.0;
+    for (long long r = ((long long)blockIdx.x * NT + threadIdx.x) >> 5; r < nrows; r += nw) {
+        const float4* row = reinterpret_cast<const float4*>(c + r * pitch);
+        float s = 0.f, e = 0.f;
+        int k = 0;
+        for (int q = lane; q < rowlen / 4; q += 32) {
+            const float4 v = EVX_IN(r * pitch + 4 * q + 3, nrows * pitch) ? row[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            two_sum_acc(s, e, v.x);
+            two_sum_acc(s, e, v.y);
+            two_sum_acc(s, e, v.z);
+            two_sum_acc(s, e, v.w);
+            if (++k == 8) {
+                acc += (double)s + (double)e;
+                s = e = 0.f;
+                k = 0;
+            }
+        }
+        acc += (double)s + (double)e;
+    }
+    acc = block_sum_double(acc, ws);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
 // The k = 0 mode of a state that is spectral in y and z and real in x is the
 // x-sum of its (ky = 0, kz = 0) line: removing it subtracts the line's mean
 // from each of its n elements (stride apart). One block, FP64 sum.
@@ -755,7 +794,10 @@ cudaError_t launch_zpass(const ZPassArgs& a, int mode, cudaStream_t st, int* gri
 
 cudaError_t launch_sum_field(const float* c, long long nrows, int rowlen, long long pitch,
                              double* partials, int nblocks, cudaStream_t st) {
-    sum_rows_kernel<<<nblocks, NT, 0, st>>>(c, nrows, rowlen, pitch, partials);
+    if (rowlen % 4 == 0 && pitch % 4 == 0 && ((uintptr_t)c & 15) == 0)
+        sum_rows_vec_kernel<<<nblocks, NT, 0, st>>>(c, nrows, rowlen, pitch, partials);
+    else
+        sum_rows_kernel<<<nblocks, NT, 0, st>>>(c, nrows, rowlen, pitch, partials);
     return cudaGetLastError();
 }
 
